@@ -1,0 +1,88 @@
+/*
+ * fam_oracle.h -- plain, slow, FP64 CPU oracle for the compact FAM time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA implementation: every coefficient
+ * below is transcribed by hand from the paper (Fan & Wu, "Compact
+ * Finite-Average-Moment Schemes with Single-Step Oscillation Elimination").
+ *
+ * Layout of a state array (no ghost cells):
+ *     U[((c * nmom + m) * ny + j) * nx + i]
+ * c = conserved component (1 for scalar laws, d+2 for Euler),
+ * m = moment (0 = cell average, 1 = scaled x-moment, 2 = scaled y-moment),
+ * ny = 1 in one dimension.
+ *
+ * Parity status (see the pins in tests/test_oracle_pins.py): every function is
+ * pinned except the shock-run solution values themselves, which the paper does
+ * not print; those are covered only by invariants (conservation, OE
+ * properties) -- "parity unpinned" for shock-run values.
+ */
+#ifndef FAM_ORACLE_H
+#define FAM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_ADVECTION = 0, OR_BURGERS = 1, OR_EULER = 2 };
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_REFLECTIVE = 2, OR_BC_INFLOW = 3 };
+enum { OR_OE_NONE = 0, OR_OE_TYPE1 = 1, OR_OE_TYPE2 = 2 };
+
+typedef struct {
+  int d;              /* 1 or 2 */
+  int nx, ny;         /* ny = 1 when d = 1 */
+  double x0, x1, y0, y1;
+  int k;              /* FAM order 3..6 */
+  int eq;             /* OR_ADVECTION / OR_BURGERS / OR_EULER */
+  int bc[4];          /* x-lo, x-hi, y-lo, y-hi */
+  double inflow[4][4];/* conservative inflow state per side (averages) */
+  double gamma;       /* Euler: ratio of specific heats */
+  double ax, ay;      /* advection velocity */
+  int oe_type;        /* OR_OE_NONE / OR_OE_TYPE1 / OR_OE_TYPE2 */
+  double gamma_k;     /* OE constant; <= 0 selects the paper's default */
+  int oe_jump_q6;     /* 2D k=6: 1 = jumps of full Q6 (printed matrices), 0 = of p6 */
+} or_problem;
+
+int or_ncomp(const or_problem* P);
+int or_nmom(const or_problem* P);
+
+/* Reconstruction (App. B / App. I).  Returns the number of coefficients of
+ * the FAM-k polynomial (k in 1D; 6, 10, 15, 21 in 2D).  c must hold 6 (1D) or
+ * 23 (2D) entries; all auxiliary coefficients are filled as well. */
+int or_recon1d(int k, const double um[2], const double u0[2], const double up[2], double c[6]);
+int or_recon2d(int k, const double a[9], const double mx[9], const double my[9], double c[23]);
+double or_basis1d(int l, double xi);
+double or_basis2d(int l, double xi, double eta);
+double or_eval1d(int ncoef, const double* c, double xi);
+double or_eval2d(int ncoef, const double* c, double xi, double eta);
+
+/* Four-point Gauss-Legendre rule on [-1/2, 1/2] (weights sum to 1). */
+void or_gauss4(double node[4], double weight[4]);
+
+/* Semi-discrete right-hand side R(U) of eq. (1dSemi) / eq. (11). */
+int or_residual(const or_problem* P, const double* U, double* R);
+
+/* Maximum Rusanov wave speeds over the mesh from cell averages. */
+void or_max_speed(const or_problem* P, const double* U, double* ax, double* ay);
+
+/* Time-step rule of Sec. 4 ("Time stepping"); smooth != 0 uses dx^(k/3). */
+double or_dt(const or_problem* P, const double* U, double cfl, int smooth);
+
+/* End-of-step OE, in place (eq. 9 / eq. 1dOE_system / eq. 2dOE_system).
+ * If theta != NULL it receives the damping exponent per cell. */
+int or_oe(const or_problem* P, double dt, double* U, double* theta);
+
+/* One SSP-RK3 step (eq. 3 / eq. 12) followed by OE, in place. */
+int or_step(const or_problem* P, double* U, double dt);
+
+/* Advance to time T (last step clamped).  max_steps <= 0: unlimited.
+ * nsteps_or_T: if T <= 0, runs exactly nsteps steps instead.  Returns 0 on
+ * success, -1 on a non-finite value. */
+int or_run(const or_problem* P, double* U, double T, long nsteps, double cfl, int smooth,
+           double* t_out, long* nsteps_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

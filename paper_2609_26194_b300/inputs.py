@@ -1,0 +1,226 @@
+"""Seeded synthetic initial data for the FAM time step, as moment arrays.
+
+This module holds only input generation: it projects analytic or piecewise
+initial data onto the evolved P1 moment state (cell average and scaled first
+moments, Sec. 2.1 / Sec. 2.2 of the paper) by Gauss quadrature or closed
+forms.  It contains none of the scheme's arithmetic and is shared by the CPU
+oracle tests and the CUDA path.
+
+Layout: 1D ``U[c, m, i]``; 2D ``U[c, m, j, i]`` with m = 0 average, 1 scaled
+x-moment (1/|I| int u (x-x_i)/dx), 2 scaled y-moment.  Euler variables are
+conservative: (rho, rho u, E) in 1D, (rho, rho u, rho v, E) in 2D.
+
+Workload recipes (shapes and value ranges follow the paper's tests):
+  * advection_sine: u0 = sin(2 pi x) on [0,1], exact moments (closed form).
+  * euler1d_riemann: [0,1], 8 face-snapped discontinuities, 9 states with
+    rho ~ U[0.1,2], u ~ U[-1,1], p ~ U[0.1,10]; rho multiplied by
+    (1 + 0.2 sin(32 pi x)).
+  * euler2d_smooth: [0,1]^2, rho = 1 + 0.2 sin(2 pi (x+y)), u = v = p = 1.
+  * euler2d_rectangles: [0,1]^2 background (1,0,0,1) with 64 face-snapped
+    periodic rectangles, side lengths U[N/32, N/4] cells, rho, p ~ U[0.1,5],
+    u, v ~ U[-1,1].
+  * euler2d_fourier: (1, .5, .5, 1) + 16 Fourier modes of amplitude 0.05/16
+    per primitive variable, integer wave numbers in [-4,4]^2 \\ {0}.
+  * batched_1d: instances with N = round(exp(U[ln 64, ln 16384])) and
+    k ~ U{3,4,5,6}, each with euler1d_riemann data (seed + i).
+  * smooth accuracy data of the paper's Examples 4.1 and 4.2.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def gauss_legendre_unit(nq: int) -> tuple[np.ndarray, np.ndarray]:
+    """Gauss-Legendre nodes on [-1/2, 1/2] and weights summing to one."""
+    x, w = np.polynomial.legendre.leggauss(nq)
+    return 0.5 * x, 0.5 * w
+
+
+# --------------------------------------------------------------------------
+# generic projections
+# --------------------------------------------------------------------------
+
+def project_1d(func, n: int, x0: float, x1: float, nq: int = 8) -> np.ndarray:
+    """Average and scaled first moment of func (returns (ncomp, npts)) per cell."""
+    dx = (x1 - x0) / n
+    xi, w = gauss_legendre_unit(nq)
+    xc = x0 + (np.arange(n) + 0.5) * dx
+    X = xc[:, None] + dx * xi[None, :]                      # (n, nq)
+    F = np.asarray(func(X.reshape(-1)), dtype=np.float64)   # (ncomp, n*nq)
+    F = F.reshape(F.shape[0], n, nq)
+    avg = np.einsum("cnq,q->cn", F, w)
+    mom = np.einsum("cnq,q->cn", F, w * xi)
+    return np.ascontiguousarray(np.stack([avg, mom], axis=1))
+
+
+def project_2d(func, nx: int, ny: int, box=(0.0, 1.0, 0.0, 1.0), nq: int = 4,
+               rows_per_chunk: int = 128) -> np.ndarray:
+    """Average and both scaled first moments of func(X, Y) -> (ncomp, ...)."""
+    x0, x1, y0, y1 = box
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    xi, w = gauss_legendre_unit(nq)
+    xc = x0 + (np.arange(nx) + 0.5) * dx
+    out = None
+    for r0 in range(0, ny, rows_per_chunk):
+        r1 = min(ny, r0 + rows_per_chunk)
+        yc = y0 + (np.arange(r0, r1) + 0.5) * dy
+        X = (xc[None, :, None, None] + dx * xi[None, None, None, :])      # (1, nx, 1, qx)
+        Y = (yc[:, None, None, None] + dy * xi[None, None, :, None])      # (rows, 1, qy, 1)
+        X, Y = np.broadcast_arrays(X, Y)                                   # (rows, nx, qy, qx)
+        F = np.asarray(func(X, Y), dtype=np.float64)                       # (nc, rows, nx, qy, qx)
+        if out is None:
+            out = np.empty((F.shape[0], 3, ny, nx), dtype=np.float64)
+        ww = w[:, None] * w[None, :]                                       # (qy, qx)
+        out[:, 0, r0:r1] = np.einsum("crnab,ab->crn", F, ww)
+        out[:, 1, r0:r1] = np.einsum("crnab,ab->crn", F, ww * xi[None, :])
+        out[:, 2, r0:r1] = np.einsum("crnab,ab->crn", F, ww * xi[:, None])
+    return np.ascontiguousarray(out)
+
+
+def primitive_to_conservative_1d(rho, u, p, gamma=GAMMA):
+    return np.stack([rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u])
+
+
+def primitive_to_conservative_2d(rho, u, v, p, gamma=GAMMA):
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+
+def advection_sine(n: int = 200) -> np.ndarray:
+    """Exact moments of sin(2 pi x) on [0,1] (closed-form integrals)."""
+    dx = 1.0 / n
+    xl = np.arange(n) * dx
+    xr = xl + dx
+    xc = xl + 0.5 * dx
+    a = 2.0 * np.pi
+    avg = (np.cos(a * xl) - np.cos(a * xr)) / (a * dx)
+
+    def prim(x):  # antiderivative of sin(a x) (x - xc)
+        return -(x - xc) * np.cos(a * x) / a + np.sin(a * x) / (a * a)
+
+    mom = (prim(xr) - prim(xl)) / (dx * dx)
+    return np.ascontiguousarray(np.stack([avg, mom])[None])
+
+
+def euler1d_riemann(n: int = 65536, seed: int = 2, gamma: float = GAMMA) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    faces = np.sort(rng.choice(np.arange(1, n), size=min(8, n - 1), replace=False))
+    ns = len(faces) + 1
+    rho_s = rng.uniform(0.1, 2.0, ns)
+    u_s = rng.uniform(-1.0, 1.0, ns)
+    p_s = rng.uniform(0.1, 10.0, ns)
+    dx = 1.0 / n
+    # piece index of every cell (faces are snapped to cell faces)
+    piece = np.searchsorted(faces, np.arange(n), side="right")
+
+    def func(x):
+        cell = np.minimum((x / dx).astype(np.int64), n - 1)
+        pc = piece[cell]
+        rho = rho_s[pc] * (1.0 + 0.2 * np.sin(32.0 * np.pi * x))
+        return primitive_to_conservative_1d(rho, u_s[pc], p_s[pc], gamma)
+
+    return project_1d(func, n, 0.0, 1.0, nq=8)
+
+
+def _sincos_moments(n: int, x0: float, x1: float, freq: float, phase: float = 0.0):
+    """1D cell averages and scaled moments of sin(freq x + phase), cos(...)."""
+    s = project_1d(lambda x: np.stack([np.sin(freq * x + phase), np.cos(freq * x + phase)]), n, x0, x1, 8)
+    return s[0, 0], s[0, 1], s[1, 0], s[1, 1]  # As, Ms, Ac, Mc
+
+
+def euler2d_smooth(n: int = 4096, gamma: float = GAMMA, box=(0.0, 1.0, 0.0, 1.0),
+                   amp: float = 0.2, freq: float = 2.0 * np.pi, u: float = 1.0, v: float = 1.0,
+                   p: float = 1.0) -> np.ndarray:
+    """rho = 1 + amp sin(freq (x + y)), constant u, v, p (separable, exact)."""
+    x0, x1, y0, y1 = box
+    Asx, Msx, Acx, Mcx = _sincos_moments(n, x0, x1, freq)
+    Asy, Msy, Acy, Mcy = _sincos_moments(n, y0, y1, freq)
+    # sin(a + b) = sin a cos b + cos a sin b
+    avg = 1.0 + amp * (Asx[None, :] * Acy[:, None] + Acx[None, :] * Asy[:, None])
+    mx = amp * (Msx[None, :] * Acy[:, None] + Mcx[None, :] * Asy[:, None])
+    my = amp * (Asx[None, :] * Mcy[:, None] + Acx[None, :] * Msy[:, None])
+    rho = np.stack([avg, mx, my])
+    e_const = p / (gamma - 1.0)
+    ke = 0.5 * (u * u + v * v)
+    E = ke * rho
+    E[0] += e_const
+    return np.ascontiguousarray(np.stack([rho, u * rho, v * rho, E]))
+
+
+def euler2d_rectangles(n: int = 4096, seed: int = 3, nrect: int = 64,
+                       gamma: float = GAMMA) -> np.ndarray:
+    """Piecewise-constant periodic rectangles painted in order (moments vanish)."""
+    rng = np.random.default_rng(seed)
+    prim = np.empty((4, n, n))
+    prim[0], prim[1], prim[2], prim[3] = 1.0, 0.0, 0.0, 1.0
+    lo, hi = max(1, n // 32), max(2, n // 4)
+    for _ in range(nrect):
+        i0, j0 = rng.integers(0, n, 2)
+        wx, wy = rng.integers(lo, hi + 1, 2)
+        st = (rng.uniform(0.1, 5.0), rng.uniform(-1.0, 1.0), rng.uniform(-1.0, 1.0), rng.uniform(0.1, 5.0))
+        ii = (i0 + np.arange(wx)) % n
+        jj = (j0 + np.arange(wy)) % n
+        for c in range(4):
+            prim[c][np.ix_(jj, ii)] = st[c]
+    cons = primitive_to_conservative_2d(prim[0], prim[1], prim[2], prim[3], gamma)
+    U = np.zeros((4, 3, n, n))
+    U[:, 0] = cons
+    return U
+
+
+def euler2d_fourier(n: int = 1024, seed: int = 5, nmodes: int = 16, amp: float = 0.05,
+                    gamma: float = GAMMA) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    base = (1.0, 0.5, 0.5, 1.0)
+    modes = []
+    for var in range(4):
+        ms = []
+        while len(ms) < nmodes:
+            kx, ky = rng.integers(-4, 5, 2)
+            if kx == 0 and ky == 0:
+                continue
+            ms.append((int(kx), int(ky), rng.uniform(0.0, 2.0 * np.pi)))
+        modes.append(ms)
+
+    def func(X, Y):
+        prim = []
+        for var in range(4):
+            f = np.full(X.shape, base[var])
+            for kx, ky, ph in modes[var]:
+                f = f + (amp / nmodes) * np.sin(2.0 * np.pi * (kx * X + ky * Y) + ph)
+            prim.append(f)
+        return primitive_to_conservative_2d(*prim, gamma=gamma)
+
+    return project_2d(func, n, n, nq=4)
+
+
+def batched_1d(n_inst: int = 4096, seed: int = 4, nmin: int = 64, nmax: int = 16384):
+    """List of (k, U) instances; U follows euler1d_riemann with seed + i."""
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_inst))).astype(int)
+    ks = rng.integers(3, 7, n_inst)
+    return [(int(ks[i]), euler1d_riemann(int(ns[i]), seed + i)) for i in range(n_inst)]
+
+
+# smooth accuracy data (Example 4.1 and Example 4.2 of the paper)
+
+def burgers_smooth(n: int) -> np.ndarray:
+    """u0 = 0.5 + sin(pi x) on [0,2]."""
+    return project_1d(lambda x: (0.5 + np.sin(np.pi * x))[None], n, 0.0, 2.0, nq=8)
+
+
+def euler1d_smooth(n: int, gamma: float = GAMMA) -> np.ndarray:
+    """(rho, u, p) = (1 + 0.2 sin(pi x), 1, 1) on [0,2]."""
+    return project_1d(lambda x: primitive_to_conservative_1d(1.0 + 0.2 * np.sin(np.pi * x),
+                                                             np.ones_like(x), np.ones_like(x), gamma),
+                      n, 0.0, 2.0, nq=8)
+
+
+def euler2d_smooth_accuracy(n: int, gamma: float = GAMMA) -> np.ndarray:
+    """(rho, u, v, p) = (1 + 0.2 sin(pi (x+y)), 1, 1, 1) on [0,2]^2."""
+    return euler2d_smooth(n, gamma, box=(0.0, 2.0, 0.0, 2.0), freq=np.pi)
