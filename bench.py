@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the FAM time step on B300.
+
+Workload (default): 2D Euler (gamma = 1.4), FAM5, periodic 4096 x 4096 grid,
+smooth density wave rho = 1 + 0.2 sin(2 pi (x + y)), u = v = p = 1, FP64,
+CFL 0.55, Type-II OE after every step.  One "step" = one full time step:
+three SSP-RK3 stage kernels + the OE kernel (with the fused CFL reduction).
+Metric: cell-stage updates per second (cells x 3 stages x steps / time).
+
+Arms:
+  --impl fam        (default) the CUDA library through its C ABI.
+  --impl reference  the FP64 CPU oracle on the host cores, each step one
+                    oracle time step on a bounded sub-grid sample of the
+                    same workload (rank 0 only).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one independent replica per GPU ("replicas only":
+the FAM step has no cross-GPU exchange in this build), barrier + max over
+ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D Euler k=5 cell-stage updates/s"
+UNIT = "cell-stage/s"
+
+# Algorithmic FP64 work per cell and stage of the stage kernel: the executed
+# DFMA / DADD / DMUL instructions of one launch (ncu, 2048^2 FAM5; see
+# profiles/stage2d_k5_f64.md) per cell -- 1139 DFMA + 426 DADD + 511 DMUL =
+# 3215 FLOP with a DFMA counted as 2 -- minus the ~200 FLOP per cell that the
+# ring of cells around each 32x8 tile spends recomputing face traces.
+FLOP_PER_CELL_STAGE = {(5, 64): 3015.0}
+# DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
+# dram__bytes_write.sum from the same capture, 1.184 GB / 4.19 M cells);
+# traffic grows with the cell count, so it scales to the 4096^2 launch.
+DRAM_BYTES_PER_CELL = {(5, 64): 282.4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fam", choices=["fam", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--precision", type=int, default=64, choices=[64, 32])
+    ap.add_argument("--cfl", type=float, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"2D Euler FAM{a.k} periodic {a.n}x{a.n}, smooth density wave "
+                        f"rho=1+0.2sin(2pi(x+y)), u=v=p=1, CFL {cfl_of(a)}, Type-II OE",
+            "grid": [a.n, a.n], "k": a.k, "equation": "euler2d", "gamma": 1.4, "oe": "type2",
+            "cells": a.n * a.n, "bytes_per_state": 4 * 3 * a.n * a.n * (a.precision // 8),
+            "l2": "state buffers (>= 1.6 GB) far larger than L2; no flush needed"}
+
+
+def cfl_of(a):
+    if a.cfl is not None:
+        return a.cfl
+    return 0.4 if a.k <= 4 else 0.55
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * (mx or max(sm))] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# oracle (CPU) baseline
+# --------------------------------------------------------------------------
+def oracle_rate(a, target_s: float, steps: int | None = None, sample_n: int = 256):
+    """Cell-stage/s of the FP64 oracle on a sample_n x sample_n sub-grid of the
+    workload (same mesh width), all host cores."""
+    import oracle
+    from paper_2609_26194_b300 import inputs
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    full_n = a.n
+    U = inputs.euler2d_smooth(full_n)[:, :, :sample_n, :sample_n].copy() if full_n <= 4096 else None
+    dx = 1.0 / full_n
+    P = oracle.Problem(d=2, nx=sample_n, ny=sample_n, x0=0.0, x1=dx * sample_n, y0=0.0, y1=dx * sample_n,
+                       k=a.k, eq=oracle.EULER)
+    dt = oracle.dt(P, U, cfl_of(a))
+    oracle.step(P, U, dt)  # warm-up (loads the library)
+    t0 = time.perf_counter()
+    n = 0
+    times = []
+    while True:
+        s0 = time.perf_counter()
+        U = oracle.step(P, U, dt)
+        times.append(time.perf_counter() - s0)
+        n += 1
+        if (steps is not None and n >= steps) or (steps is None and time.perf_counter() - t0 >= target_s):
+            break
+    el = time.perf_counter() - t0
+    return {"value": 3.0 * sample_n * sample_n * n / el, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{n} oracle time steps (3 stages + OE) on a {sample_n}x{sample_n} periodic sub-grid of the "
+                      f"{full_n}x{full_n} FAM{a.k} workload, {el:.1f} s"}, times
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps, warm = a.steps, a.warmup
+    # each step: one oracle step on a 256 x 256 sample of the workload
+    base, _ = oracle_rate(a, 0, steps=warm + steps)
+    _, times = oracle_rate(a, 0, steps=warm + steps)
+    t = sum(times[warm:])
+    val = 3.0 * 256 * 256 * steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": f"each step: one oracle time step on a 256x256 periodic sub-grid of the "
+                                       f"{a.n}x{a.n} workload"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_fam(a):
+    import torch
+    from paper_2609_26194_b300 import fam, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n, k, prec = a.n, a.k, a.precision
+    cfl = cfl_of(a)
+    U = inputs.euler2d_smooth(n)
+    if prec == 32:
+        U = U.astype(np.float32)
+    # a dedicated stream shared by the library's launches and the CUDA events
+    # (torch's default stream is the legacy NULL stream, handle 0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = fam.Solver(2, n, n, k=k, equation=fam.EULER, bc=fam.PERIODIC, precision=prec,
+                   stream=stream.cuda_stream)
+    dev = torch.from_numpy(U).cuda()
+    s.set_state(dev)
+    for _ in range(a.warmup):
+        s.step(cfl)
+    s.sync()
+    s.set_option("profile", 1)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        s.step(cfl)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop() if clocks else None
+    s.sync()
+    kern_ms, prof_steps = s.profile()
+    ms = max_over_ranks(ms)
+    cells = n * n
+    value = world * 3.0 * cells * a.steps / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: per step, H2D of the
+    # state from pinned memory, one FAM step, D2H of the state
+    host_in = torch.from_numpy(U).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    s.set_option("profile", 0)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        s.set_state(host_in.numpy())
+        s.step(cfl)
+        s.get_state(host_out.numpy())
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    state_bytes = U.nbytes
+    e2e = {"value": world * 3.0 * cells * a.e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+
+    # roofline of the dominant kernel (the stage kernel)
+    peak_flops = fam.alu_peak(prec)
+    stage_ms = sum(kern_ms[:3]) / max(1, 3 * prof_steps)
+    oe_ms = kern_ms[3] / max(1, prof_steps)
+    fpc = FLOP_PER_CELL_STAGE.get((k, prec))
+    traffic = DRAM_BYTES_PER_CELL.get((k, prec))
+    if fpc is not None:
+        achieved = fpc * cells / (stage_ms * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak_flops, "traffic": (traffic * cells if traffic else None),
+                "peak_source": f"measured FP{prec} FMA loop on this GPU (fam_alu_peak), live in this run",
+                "kernel": "stage2d", "kernel_ms": stage_ms}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": "stage2d", "kernel_ms": stage_ms}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    alg_bytes = 8.0 / 3.0 * 12 * (prec // 8)  # 8 state passes per step, per cell-stage
+    hbm_roof = {"algorithmic_bytes_per_cell_stage": alg_bytes,
+                "achieved_gbs": alg_bytes * value / world / 1e9, "peak_gbs": hbm,
+                "frac": alg_bytes * value / world / 1e9 / hbm,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6400 GB/s"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32",
+            "data": "synthetic (seeded analytic initial data, exact moments)",
+            "config": {**workload_config(a), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "hbm_roofline": hbm_roof,
+            "kernel_ms": {"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
+                          "stage3": kern_ms[2] / max(1, prof_steps), "oe": oe_ms},
+            "e2e": e2e, "gpu_launches": 4 * a.steps, "clocks": ck}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb, _ = oracle_rate(a, 15.0)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_fam(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

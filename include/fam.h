@@ -1,0 +1,204 @@
+/*
+ * fam.h -- C ABI of the B300 (sm_103a) library for the time step of the
+ * compact finite-average-moment (FAM) schemes with single-step oscillation
+ * elimination (Fan & Wu, "Compact Finite-Average-Moment Schemes with
+ * Single-Step Oscillation Elimination for Hyperbolic Conservation Laws").
+ *
+ * Problem statement (Sec. 2.1, eq. 1dHCLS; Sec. 2.2, eq. 10): a scalar law or
+ * the Euler equations (Sec. 2.3) on a uniform Cartesian mesh of [x0,x1] or
+ * [x0,x1]x[y0,y1], order k = 3..6, boundary condition, end time T and CFL
+ * number (Sec. 4, "Time stepping").  The evolved state is the P1 moment
+ * state: per cell and conserved component the cell average and the scaled
+ * first moment(s) (Sec. 2.1 / 2.2).
+ *
+ * STATE LAYOUT (all entry points that take a state): a dense array
+ *     U[c][m][j][i]    (1D: U[c][m][i])
+ * c = conserved component (scalar: 1; Euler 1D: rho, rho u, E; Euler 2D:
+ * rho, rho u, rho v, E), m = 0 cell average, 1 scaled x-moment
+ * (1/|I| int u (x-x_i)/dx), 2 scaled y-moment (2D); j = row (y), i = column
+ * (x).  Element type: double for precision 64, float for precision 32.
+ *
+ * OWNERSHIP: the library owns all device memory of a handle; buffers passed
+ * by the caller are only read or written during the call (host buffers) or
+ * during the call's stream work (device buffers).  A handle is not
+ * thread-safe.  Device pointers must be on the handle's device.
+ *
+ * ERRORS: every call returns a fam_status; no call aborts the process.
+ * fam_last_error() returns a message for the last failing call of a handle.
+ * Kernels flag non-finite states, non-physical averages (rho <= 0 or
+ * p <= 0) and bounded-wait timeouts in a device status word; fam_sync()
+ * reports them as FAM_E_NONPHYSICAL / FAM_E_TIMEOUT.
+ */
+#ifndef FAM_H
+#define FAM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fam_handle* fam_t;
+
+typedef enum {
+  FAM_OK = 0,
+  FAM_E_INVAL = 1,        /* invalid argument */
+  FAM_E_NOMEM = 2,        /* device allocation failed */
+  FAM_E_CUDA = 3,         /* CUDA runtime / driver error */
+  FAM_E_NONPHYSICAL = 4,  /* non-finite or non-physical state detected */
+  FAM_E_TIMEOUT = 5,      /* a kernel's bounded wait gave up */
+  FAM_E_STATE = 6,        /* call out of order (e.g. step before set_state) */
+  FAM_E_UNSUPPORTED = 7   /* option combination not built */
+} fam_status;
+
+typedef enum { FAM_ADVECTION = 0, FAM_BURGERS = 1, FAM_EULER = 2 } fam_equation;
+typedef enum { FAM_BC_PERIODIC = 0, FAM_BC_OUTFLOW = 1 } fam_bc;
+
+typedef struct {
+  int d;           /* dimension: 1 or 2 */
+  int nx, ny;      /* cells per direction (ny ignored for d = 1); >= 4 */
+  double x0, x1;   /* domain [x0, x1] */
+  double y0, y1;   /* domain [y0, y1] (d = 2) */
+} fam_grid;
+
+/* Create a solver.  k in {3,4,5,6} selects FAM-k (Sec. 2.4).  gamma: ratio of
+ * specific heats for FAM_EULER (the paper uses 1.4), advection speed a in
+ * both directions for FAM_ADVECTION (change per direction with the options
+ * "ax"/"ay"), ignored for FAM_BURGERS.  bc applies on every side (Remark in
+ * Sec. 2.3: periodic, or outflow ghost cells copying average and moments).
+ * precision: 64 (FP64) or 32 (FP32).  stream: a cudaStream_t to run on, or
+ * NULL for a stream the library creates.  On success *out receives the
+ * handle; the state is undefined until fam_set_state().
+ * Errors: FAM_E_INVAL (bad argument), FAM_E_NOMEM, FAM_E_CUDA. */
+fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int bc, double gamma,
+                      int precision, void* stream);
+
+/* Set an option (before or between steps).  Keys:
+ *   "oe_type"    0 = no OE, 2 = Type II (default; Tab. sigma1d / sigma2d)
+ *   "gamma_k"    OE constant; <= 0 restores the paper's defaults (1D: 25 for
+ *                k = 3,4 and 12.5 for k = 5,6; 2D: 25 and 15; Sec. 2.1/2.2)
+ *   "oe_jump_q6" 2D k = 6 only: 1 (default) takes the OE jumps from the full
+ *                auxiliary Q6, which reproduces the printed jump matrices
+ *                (App. J); 0 takes them from p6 = Pi_5 Q6
+ *   "smooth_dt"  1: time step with dx^(k/3) (smooth runs, Sec. 4); 0: dx
+ *   "ax", "ay"   advection speeds (FAM_ADVECTION)
+ *   "dt_max"     upper bound on the step size (<= 0: none)
+ *   "profile"    1: fam_step() brackets each of its four kernel launches with
+ *                CUDA events (read with fam_profile); setting it resets the
+ *                accumulated times
+ * Errors: FAM_E_INVAL (unknown key or value), FAM_E_UNSUPPORTED. */
+fam_status fam_set_option(fam_t h, const char* key, double value);
+
+/* Copy a state in (layout above).  on_device = 0: U is host memory;
+ * 1: U is device memory of the handle's device.  Resets the clock to t = 0
+ * and the step counter to 0.  Synchronous for host memory. */
+fam_status fam_set_state(fam_t h, const void* U, int on_device);
+
+/* Copy the current state out (layout above).  Synchronous for host memory;
+ * for device memory the copy is ordered on the handle's stream. */
+fam_status fam_get_state(fam_t h, void* U, int on_device);
+
+/* Enqueue one time step (Alg. 1): the three SSP-RK3 stages of eq. (3)/(12)
+ * and the end-of-step OE (eq. 9 / eq. 2dOE_sol, system forms of Sec. 2.3).
+ * The step size follows the CFL rule of Sec. 4 from the maximum Rusanov
+ * speed at the current cell averages, computed on the device (no host
+ * synchronisation).  Asynchronous; call fam_sync() to wait and check. */
+fam_status fam_step(fam_t h, double cfl);
+
+/* Enqueue exactly nsteps steps as one CUDA graph launch (captured once per
+ * distinct nsteps and replayed).  Asynchronous. */
+fam_status fam_run_steps(fam_t h, long nsteps, double cfl);
+
+/* Advance to time T (the last step is shortened to land on T), at most
+ * max_steps steps if max_steps > 0.  Synchronous.  *nsteps_out (may be NULL)
+ * receives the number of steps taken by this call. */
+fam_status fam_run(fam_t h, double T, double cfl, long max_steps, long* nsteps_out);
+
+/* Wait for the handle's stream and report device-side status flags. */
+fam_status fam_sync(fam_t h);
+
+/* Current time, size of the next step and number of steps taken (any may be
+ * NULL).  Synchronous. */
+fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps);
+
+/* Per-kernel device time accumulated over the profiled fam_step() calls since
+ * the option "profile" was last set: ms[0..2] = stage 1..3 kernels, ms[3] =
+ * OE kernel (milliseconds, CUDA events on the handle's stream); *nsteps =
+ * number of profiled steps.  Synchronises the stream. */
+fam_status fam_profile(fam_t h, double* ms, long* nsteps);
+
+/* Semi-discrete right-hand side R(U) of eq. (1dSemi) / eq. (11) for the
+ * state U (layout above), written to R (same layout).  Uses the handle's
+ * scratch buffers; the handle's current state is not changed. */
+fam_status fam_residual(fam_t h, const void* U, void* R, int on_device);
+
+/* The OE operator alone with step size dt (eq. 9 / eq. 2dOE_sol with the
+ * Type-II coefficient): Uout = F_OE(U).  Averages are copied unchanged.
+ * The handle's current state is not changed. */
+fam_status fam_oe(fam_t h, double dt, const void* U, void* Uout, int on_device);
+
+/* Message of the last failing call on h (never NULL). */
+const char* fam_last_error(fam_t h);
+
+/* Name of a status code. */
+const char* fam_status_string(fam_status s);
+
+/* Release all resources of h (NULL is ignored). */
+void fam_destroy(fam_t h);
+
+/* ------------------------------------------------------------------------
+ * Batched 1D problems (not in the paper: many independent instances in one
+ * persistent launch).  Instance i has nx[i] cells on [x0, x1] and order
+ * k[i]; all share the equation, bc, gamma (see fam_create) and precision.
+ * State layout: the instances' 1D states (U_i[c][m][i]) concatenated in
+ * instance order.  Each instance takes its own CFL step size (Sec. 4) from
+ * its own maximum Rusanov speed.  The per-tile arithmetic is the
+ * single-problem code, so each instance evolves exactly as fam_step would.
+ * ------------------------------------------------------------------------ */
+typedef struct fam_batch* fam_batch_t;
+
+/* Errors: FAM_E_INVAL (bad sizes/orders), FAM_E_NOMEM, FAM_E_CUDA. */
+fam_status fam_batch_create(fam_batch_t* out, int n_inst, const int* nx, const int* k, double x0, double x1,
+                            int equation, int bc, double gamma, int precision, void* stream);
+/* Keys: "oe_type" (0 / 2), "gamma_k" (<= 0: defaults per order), "ax",
+ * "tile_x" (64 / 128 / 256 cells per tile), "blocks_per_sm" (<= 0: the
+ * occupancy maximum). */
+fam_status fam_batch_set_option(fam_batch_t h, const char* key, double value);
+/* Copy the concatenated state in / out (on_device as in fam_set_state);
+ * set_state resets every instance's clock. */
+fam_status fam_batch_set_state(fam_batch_t h, const void* U, int on_device);
+fam_status fam_batch_get_state(fam_batch_t h, void* U, int on_device);
+/* Advance every instance by nsteps steps (eq. 3/12 + OE) in ONE cooperative
+ * persistent kernel launch (a tile work list walked pass by pass with
+ * bounded grid barriers), captured in a CUDA graph per (nsteps, cfl).
+ * Asynchronous; fam_batch_sync() waits and reports device flags. */
+fam_status fam_batch_run(fam_batch_t h, long nsteps, double cfl);
+fam_status fam_batch_sync(fam_batch_t h);
+/* Per-instance time, next step size and steps taken (arrays of n_inst; any
+ * may be NULL).  Synchronous. */
+fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps);
+/* Launch shape: tile width, blocks of the persistent grid, tiles, cells. */
+fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, long* cells);
+/* Autotuner: times probe_steps steps for each tile width (64, 128, 256) and
+ * blocks-per-SM choice on the handle's current state (restored afterwards),
+ * keeps the fastest, and appends it to cache_path (if not NULL) keyed by GPU
+ * name and problem; a cached entry is reused without timing. */
+fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char* cache_path, int* tile_x,
+                          int* blocks_per_sm);
+const char* fam_batch_last_error(fam_batch_t h);
+void fam_batch_destroy(fam_batch_t h);
+
+/* Measured throughput of this GPU's FP64 (precision 64) or FP32 (32) fused
+ * multiply-add pipe in FLOP/s, from a register-resident FMA loop timed with
+ * CUDA events (a roofline denominator; not part of the method). */
+fam_status fam_alu_peak(int precision, double* flops_per_s);
+
+/* Diagnostics: the library's FP64 reciprocal, reciprocal square root and
+ * square root (FP32 hardware approximation refined by two Newton-Raphson
+ * steps) applied to n host values x (positive, within the FP32 normal
+ * range); results are written to the three host arrays.  Test hook for
+ * comparing against correctly rounded results. */
+fam_status fam_selftest_math(const double* x, int n, double* rcp, double* rsqrt, double* sqrt_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FAM_H */

@@ -1,0 +1,508 @@
+// fam_api.cu -- host side of the FAM C ABI (include/fam.h).
+//
+// A handle owns three padded state buffers (A: state, B and C: stage
+// buffers), a device control block (time, step size, speed reduction,
+// status) and one TMA descriptor per buffer.  One step is
+//   stage 1: A -> B,  stage 2: B -> C,  stage 3: C -> B,  OE: B -> A,
+// with U^{n,0} = A read by stages 2 and 3 (eq. 12).  The step size lives on
+// the device, so steps need no host synchronisation and are captured into
+// CUDA graphs.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "fam_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// tensor-map encoding through the driver entry point (no link to libcuda)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+static bool pick(fam_handle* h) {
+#define FAM_PK(D, P, K) \
+  if (h->d == D && h->prec == P && h->k == K) return fam_pick_d##D##_p##P##_k##K(h);
+#define FAM_PKK(D, P) FAM_PK(D, P, 3) FAM_PK(D, P, 4) FAM_PK(D, P, 5) FAM_PK(D, P, 6)
+  FAM_PKK(1, 64) FAM_PKK(1, 32) FAM_PKK(2, 64) FAM_PKK(2, 32)
+#undef FAM_PKK
+#undef FAM_PK
+  return false;
+}
+
+// ghost fill of a freshly uploaded state (reads interior, writes images)
+template <typename T>
+__global__ void fill_ghosts_kernel(T* U, const Geo geo, int np) {
+  const long long n = (long long)geo.nx * geo.ny * np;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % geo.nx);
+    const long long r = q / geo.nx;
+    const int j = (int)(r % geo.ny);
+    const int p = (int)(r / geo.ny);
+    const T v = U[cell_index(geo, p, j, i)];
+    store_with_ghosts(U, geo, p, j, i, v);
+  }
+}
+
+static fam_status fill_ghosts(fam_handle* h, int b) {
+  long long n = (long long)h->geo.nx * h->geo.ny * h->np;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+  if (h->prec == 64)
+    fill_ghosts_kernel<double><<<blocks, 256, 0, h->stream>>>(bufp<double>(h, b), h->geo, h->np);
+  else
+    fill_ghosts_kernel<float><<<blocks, 256, 0, h->stream>>>(bufp<float>(h, b), h->geo, h->np);
+  FAM_CUDA(h, cudaGetLastError());
+  return FAM_OK;
+}
+
+static fam_status encode_maps(fam_handle* h) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return fail(h, FAM_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+  CUtensorMapDataType dt = h->prec == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (int b = 0; b < 3; ++b) {
+    CUresult r;
+    if (h->d == 2) {
+      cuuint64_t dims[3] = {(cuuint64_t)h->geo.px, (cuuint64_t)h->geo.rows, (cuuint64_t)h->np};
+      cuuint64_t strides[2] = {(cuuint64_t)h->geo.px * h->elem, (cuuint64_t)h->geo.plane * h->elem};
+      cuuint32_t box[3] = {TX2 + 4, TY2 + 4, (cuuint32_t)h->np};
+      cuuint32_t es[3] = {1, 1, 1};
+      r = enc(&h->tm[b], dt, 3, h->buf[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      cuuint64_t dims[2] = {(cuuint64_t)h->geo.px, (cuuint64_t)h->np};
+      cuuint64_t strides[1] = {(cuuint64_t)h->geo.plane * h->elem};
+      cuuint32_t box[2] = {TX1 + 4, (cuuint32_t)h->np};
+      cuuint32_t es[2] = {1, 1};
+      r = enc(&h->tm[b], dt, 2, h->buf[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return fail(h, FAM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+  }
+  return FAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// control block
+// ---------------------------------------------------------------------------
+static fam_status ctl_read(fam_handle* h, FamCtl* out) {
+  FAM_CUDA(h, cudaMemcpyAsync(out, h->ctl, sizeof(FamCtl), cudaMemcpyDeviceToHost, h->stream));
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return FAM_OK;
+}
+
+// (Re)compute the step size from the current state A (no time advance).
+static fam_status refresh_dt(fam_handle* h, double cfl, double T, bool reset_clock) {
+  FamCtl c;
+  fam_status s = ctl_read(h, &c);
+  if (s) return s;
+  if (reset_clock) {
+    c.t = 0.0;
+    c.step = 0;
+    c.status = 0;
+  }
+  c.cfl = cfl;
+  c.T = T;
+  c.dt_max = h->dt_max;
+  c.dt = 0.0;
+  c.final_step = 0;
+  c.dim = h->d;
+  c.dx = h->geo.dx;
+  c.dy = h->geo.dy;
+  const double e = h->smooth_dt ? h->k / 3.0 : 1.0;
+  c.dxe = std::pow(h->geo.dx, e);
+  c.dye = std::pow(h->geo.dy, e);
+  c.alpha_bits[0] = c.alpha_bits[1] = 0ull;
+  c.blocks_done = 0;
+  FAM_CUDA(h, cudaMemcpyAsync(h->ctl, &c, sizeof(FamCtl), cudaMemcpyHostToDevice, h->stream));
+  FAM_CUDA(h, h->ops.alpha(h, 0));
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->cfl_set = cfl;
+  h->T_set = T;
+  h->dt_valid = true;
+  return FAM_OK;
+}
+
+static fam_status enqueue_step(fam_handle* h) {
+  FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
+  FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
+  FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
+  FAM_CUDA(h, h->ops.oe(h, 1, 0, -1.0));
+  return FAM_OK;
+}
+
+static cudaEvent_t next_event(fam_handle* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// fam_step with CUDA events around each of the four launches
+static fam_status enqueue_step_profiled(fam_handle* h) {
+  cudaEvent_t e[5];
+  for (int q = 0; q < 5; ++q) {
+    e[q] = next_event(h);
+    if (!e[q]) return fail(h, FAM_E_CUDA, "cudaEventCreate failed");
+  }
+  FAM_CUDA(h, cudaEventRecord(e[0], h->stream));
+  FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
+  FAM_CUDA(h, cudaEventRecord(e[1], h->stream));
+  FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
+  FAM_CUDA(h, cudaEventRecord(e[2], h->stream));
+  FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
+  FAM_CUDA(h, cudaEventRecord(e[3], h->stream));
+  FAM_CUDA(h, h->ops.oe(h, 1, 0, -1.0));
+  FAM_CUDA(h, cudaEventRecord(e[4], h->stream));
+  return FAM_OK;
+}
+
+static fam_status ensure_dt(fam_handle* h, double cfl, double T) {
+  if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
+  if (!(cfl > 0.0)) return fail(h, FAM_E_INVAL, "cfl must be positive");
+  if (!h->dt_valid || cfl != h->cfl_set || T != h->T_set) return refresh_dt(h, cfl, T, false);
+  return FAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* fam_status_string(fam_status s) {
+  switch (s) {
+    case FAM_OK: return "FAM_OK";
+    case FAM_E_INVAL: return "FAM_E_INVAL";
+    case FAM_E_NOMEM: return "FAM_E_NOMEM";
+    case FAM_E_CUDA: return "FAM_E_CUDA";
+    case FAM_E_NONPHYSICAL: return "FAM_E_NONPHYSICAL";
+    case FAM_E_TIMEOUT: return "FAM_E_TIMEOUT";
+    case FAM_E_STATE: return "FAM_E_STATE";
+    case FAM_E_UNSUPPORTED: return "FAM_E_UNSUPPORTED";
+  }
+  return "FAM_E_?";
+}
+
+const char* fam_last_error(fam_t h) { return h ? h->err.c_str() : "null handle"; }
+
+void fam_destroy(fam_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  for (int b = 0; b < 3; ++b)
+    if (h->buf[b]) cudaFree(h->buf[b]);
+  if (h->ctl) cudaFree(h->ctl);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int bc, double gamma, int precision,
+                      void* stream) {
+  if (!out || !grid) return FAM_E_INVAL;
+  *out = nullptr;
+  if (grid->d != 1 && grid->d != 2) return FAM_E_INVAL;
+  if (k < 3 || k > 6) return FAM_E_INVAL;
+  if (equation < FAM_ADVECTION || equation > FAM_EULER) return FAM_E_INVAL;
+  if (bc != FAM_BC_PERIODIC && bc != FAM_BC_OUTFLOW) return FAM_E_INVAL;
+  if (precision != 64 && precision != 32) return FAM_E_INVAL;
+  if (grid->nx < 4 || (grid->d == 2 && grid->ny < 4)) return FAM_E_INVAL;
+  if (!(grid->x1 > grid->x0) || (grid->d == 2 && !(grid->y1 > grid->y0))) return FAM_E_INVAL;
+  if (equation == FAM_EULER && !(gamma > 1.0)) return FAM_E_INVAL;
+  fam_handle* h = new fam_handle();
+  h->d = grid->d;
+  h->k = k;
+  h->eq = equation;
+  h->bc = bc;
+  h->prec = precision;
+  h->grid = *grid;
+  h->gamma = gamma;
+  h->ax = h->ay = gamma;
+  if (equation == FAM_EULER) h->ax = h->ay = 1.0;
+  h->nc = equation == FAM_EULER ? grid->d + 2 : 1;
+  h->nm = grid->d + 1;
+  h->np = h->nc * h->nm;
+  h->elem = precision == 64 ? 8 : 4;
+  Geo& g = h->geo;
+  g.nx = grid->nx;
+  g.ny = grid->d == 2 ? grid->ny : 1;
+  g.px = ((g.nx + 2 * G) + 3) / 4 * 4;
+  g.rows = grid->d == 2 ? g.ny + 2 * G : 1;
+  g.plane = (long long)g.px * g.rows;
+  g.bcx = g.bcy = bc;
+  g.dx = (grid->x1 - grid->x0) / grid->nx;
+  g.dy = grid->d == 2 ? (grid->y1 - grid->y0) / grid->ny : 1.0;
+  g.idx = 1.0 / g.dx;
+  g.idy = 1.0 / g.dy;
+  bool ok = pick(h);
+  if (!ok) {
+    delete h;
+    return FAM_E_UNSUPPORTED;
+  }
+  const char* fault = std::getenv("FAM_FAULT_ALLOC");
+  if (fault && fault[0] == '1') {
+    delete h;
+    return FAM_E_NOMEM;
+  }
+  cudaError_t e = h->ops.prepare();
+  if (e != cudaSuccess) {
+    fam_destroy(h);
+    return FAM_E_CUDA;
+  }
+  if (stream) {
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fam_destroy(h);
+      return FAM_E_CUDA;
+    }
+    h->own_stream = true;
+  }
+  h->buf_elems = (size_t)g.plane * h->np;
+  for (int b = 0; b < 3; ++b) {
+    if (cudaMalloc(&h->buf[b], h->buf_elems * h->elem) != cudaSuccess) {
+      fam_destroy(h);
+      return FAM_E_NOMEM;
+    }
+    cudaMemsetAsync(h->buf[b], 0, h->buf_elems * h->elem, h->stream);
+  }
+  if (cudaMalloc(&h->ctl, sizeof(FamCtl)) != cudaSuccess) {
+    fam_destroy(h);
+    return FAM_E_NOMEM;
+  }
+  cudaMemsetAsync(h->ctl, 0, sizeof(FamCtl), h->stream);
+  if (encode_maps(h) != FAM_OK) {
+    fam_destroy(h);
+    return FAM_E_CUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    fam_destroy(h);
+    return FAM_E_CUDA;
+  }
+  *out = h;
+  return FAM_OK;
+}
+
+fam_status fam_set_option(fam_t h, const char* key, double v) {
+  if (!h || !key) return FAM_E_INVAL;
+  std::string k(key);
+  if (k == "oe_type") {
+    if (v == 0.0 || v == 2.0) h->oe_type = (int)v;
+    else if (v == 1.0) return fail(h, FAM_E_UNSUPPORTED, "Type-I OE is not built in the CUDA path");
+    else return fail(h, FAM_E_INVAL, "oe_type must be 0 or 2");
+  } else if (k == "gamma_k") {
+    h->gamma_k = v;
+  } else if (k == "oe_jump_q6") {
+    h->oe_q6 = v != 0.0;
+  } else if (k == "smooth_dt") {
+    h->smooth_dt = v != 0.0;
+  } else if (k == "ax") {
+    h->ax = v;
+  } else if (k == "ay") {
+    h->ay = v;
+  } else if (k == "dt_max") {
+    h->dt_max = v;
+  } else if (k == "profile") {
+    h->profile = v != 0.0;
+    h->ev_used = 0;
+    h->prof_steps = 0;
+    for (double& x : h->prof_ms) x = 0.0;
+    return FAM_OK;
+  } else {
+    return fail(h, FAM_E_INVAL, "unknown option " + k);
+  }
+  h->dt_valid = false;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  return FAM_OK;
+}
+
+static fam_status copy_in(fam_handle* h, const void* U, int on_device, int b) {
+  if (!U) return fail(h, FAM_E_INVAL, "null state pointer");
+  const Geo& g = h->geo;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const char* src = reinterpret_cast<const char*>(U);
+  char* dst = reinterpret_cast<char*>(h->buf[b]);
+  const size_t row = (size_t)g.nx * h->elem;
+  const size_t src_plane = row * g.ny;
+  for (int p = 0; p < h->np; ++p) {
+    char* d0 = dst + ((size_t)p * g.plane + (size_t)(h->d == 2 ? G : 0) * g.px + G) * h->elem;
+    FAM_CUDA(h, cudaMemcpy2DAsync(d0, (size_t)g.px * h->elem, src + p * src_plane, row, row, g.ny, kind, h->stream));
+  }
+  return fill_ghosts(h, b);
+}
+
+static fam_status copy_out(fam_handle* h, void* U, int on_device, int b) {
+  if (!U) return fail(h, FAM_E_INVAL, "null state pointer");
+  const Geo& g = h->geo;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  char* dst = reinterpret_cast<char*>(U);
+  const char* src = reinterpret_cast<const char*>(h->buf[b]);
+  const size_t row = (size_t)g.nx * h->elem;
+  const size_t dst_plane = row * g.ny;
+  for (int p = 0; p < h->np; ++p) {
+    const char* s0 = src + ((size_t)p * g.plane + (size_t)(h->d == 2 ? G : 0) * g.px + G) * h->elem;
+    FAM_CUDA(h, cudaMemcpy2DAsync(dst + p * dst_plane, row, s0, (size_t)g.px * h->elem, row, g.ny, kind, h->stream));
+  }
+  if (!on_device) FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_set_state(fam_t h, const void* U, int on_device) {
+  if (!h) return FAM_E_INVAL;
+  fam_status s = copy_in(h, U, on_device, 0);
+  if (s) return s;
+  h->have_state = true;
+  h->dt_valid = false;
+  // reset the clock; the step size is computed at the first step
+  FamCtl c;
+  std::memset(&c, 0, sizeof(c));
+  FAM_CUDA(h, cudaMemcpyAsync(h->ctl, &c, sizeof(FamCtl), cudaMemcpyHostToDevice, h->stream));
+  if (!on_device) FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_get_state(fam_t h, void* U, int on_device) {
+  if (!h) return FAM_E_INVAL;
+  if (!h->have_state) return fail(h, FAM_E_STATE, "no state");
+  return copy_out(h, U, on_device, 0);
+}
+
+fam_status fam_step(fam_t h, double cfl) {
+  if (!h) return FAM_E_INVAL;
+  fam_status s = ensure_dt(h, cfl, h->T_set);
+  if (s) return s;
+  return h->profile ? enqueue_step_profiled(h) : enqueue_step(h);
+}
+
+fam_status fam_run_steps(fam_t h, long nsteps, double cfl) {
+  if (!h) return FAM_E_INVAL;
+  if (nsteps < 0) return fail(h, FAM_E_INVAL, "nsteps < 0");
+  fam_status s = ensure_dt(h, cfl, h->T_set);
+  if (s) return s;
+  if (nsteps == 0) return FAM_OK;
+  auto it = h->graphs.find(nsteps);
+  if (it == h->graphs.end()) {
+    cudaGraph_t graph;
+    FAM_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    fam_status es = FAM_OK;
+    for (long q = 0; q < nsteps && es == FAM_OK; ++q) es = enqueue_step(h);
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (es) return es;
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaGraphInstantiate");
+    it = h->graphs.emplace(nsteps, exec).first;
+  }
+  FAM_CUDA(h, cudaGraphLaunch(it->second, h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_sync(fam_t h) {
+  if (!h) return FAM_E_INVAL;
+  FamCtl c;
+  fam_status s = ctl_read(h, &c);
+  if (s) return s;
+  if (c.status & kStatusTimeout) return fail(h, FAM_E_TIMEOUT, "a kernel's bounded wait timed out");
+  if (c.status & (kStatusNonFinite | kStatusNonPhysical))
+    return fail(h, FAM_E_NONPHYSICAL, (c.status & kStatusNonFinite) ? "non-finite state" : "non-physical state");
+  return FAM_OK;
+}
+
+fam_status fam_run(fam_t h, double T, double cfl, long max_steps, long* nsteps_out) {
+  if (!h) return FAM_E_INVAL;
+  if (!(T > 0.0)) return fail(h, FAM_E_INVAL, "T must be positive");
+  fam_status s = ensure_dt(h, cfl, T);
+  if (s) return s;
+  FamCtl c;
+  s = ctl_read(h, &c);
+  if (s) return s;
+  const unsigned long long start = c.step;
+  long done = 0;
+  const long chunk = 16;
+  while (c.dt > 0.0 && (max_steps <= 0 || done < max_steps)) {
+    long n = chunk;
+    if (max_steps > 0 && max_steps - done < n) n = max_steps - done;
+    s = fam_run_steps(h, n, cfl);
+    if (s) return s;
+    s = fam_sync(h);
+    if (s) return s;
+    s = ctl_read(h, &c);
+    if (s) return s;
+    done = (long)(c.step - start);
+  }
+  if (nsteps_out) *nsteps_out = (long)(c.step - start);
+  return FAM_OK;
+}
+
+fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps) {
+  if (!h) return FAM_E_INVAL;
+  FamCtl c;
+  fam_status s = ctl_read(h, &c);
+  if (s) return s;
+  if (t) *t = c.t;
+  if (dt_next) *dt_next = c.dt;
+  if (steps) *steps = (long)c.step;
+  return FAM_OK;
+}
+
+fam_status fam_profile(fam_t h, double* ms, long* nsteps) {
+  if (!h || !ms) return FAM_E_INVAL;
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (size_t b = 0; b + 5 <= h->ev_used; b += 5) {
+    for (int q = 0; q < 4; ++q) {
+      float t = 0.f;
+      FAM_CUDA(h, cudaEventElapsedTime(&t, h->ev_pool[b + q], h->ev_pool[b + q + 1]));
+      h->prof_ms[q] += t;
+    }
+    h->prof_steps += 1;
+  }
+  h->ev_used = 0;
+  for (int q = 0; q < 4; ++q) ms[q] = h->prof_ms[q];
+  if (nsteps) *nsteps = h->prof_steps;
+  return FAM_OK;
+}
+
+fam_status fam_residual(fam_t h, const void* U, void* R, int on_device) {
+  if (!h) return FAM_E_INVAL;
+  fam_status s = copy_in(h, U, on_device, 1);
+  if (s) return s;
+  FAM_CUDA(h, h->ops.stage(h, 1, 1, 2, 0));
+  return copy_out(h, R, on_device, 2);
+}
+
+fam_status fam_oe(fam_t h, double dt, const void* U, void* Uout, int on_device) {
+  if (!h) return FAM_E_INVAL;
+  if (!(dt >= 0.0)) return fail(h, FAM_E_INVAL, "dt must be >= 0");
+  fam_status s = copy_in(h, U, on_device, 1);
+  if (s) return s;
+  FAM_CUDA(h, h->ops.oe(h, 1, 2, dt));
+  s = copy_out(h, Uout, on_device, 2);
+  if (s) return s;
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return FAM_OK;
+}
+
+}  // extern "C"

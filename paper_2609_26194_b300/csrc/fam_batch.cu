@@ -1,0 +1,684 @@
+// fam_batch.cu -- many independent 1D FAM problems in one persistent launch.
+//
+// Instances of uneven size N_i and order k_i (3..6) share three packed state
+// buffers (A state, B and C stage buffers; instance i at element offset
+// off_i, SoA planes of padded pitch px_i).  Their cells are cut into tiles of
+// TX cells; one cooperative persistent kernel walks the tile list for each
+// pass of a time step -- stage 1, 2, 3 (eq. 3 / 12) and OE (eq. 9 /
+// 1dOE_system) -- with a bounded grid barrier between passes, and a per-
+// instance step-size pass (Sec. 4 CFL rule with the instance's own maximum
+// Rusanov speed) at the end of each step.  The arithmetic per tile is the
+// same device code as the single-problem kernels (stage1d_tile,
+// oe1d_tile), so every instance evolves bit for bit as it would alone.
+//
+// Tile width and blocks per SM are chosen by fam_batch_tune(), which times
+// each candidate on the handle's own data and can cache the choice in a file.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/fam.h"
+#include "fam_kernels1d.cuh"
+
+using namespace fam;
+
+namespace {
+
+struct BatchInst {
+  long long off;  // element offset of plane 0
+  int nx, px, k, pad;
+  double dx, idx;
+  double gamma_k;
+};
+
+struct BatchCtl {
+  double dt, t;
+  unsigned long long alpha_bits;
+  unsigned long long steps;
+};
+
+struct BatchGlobal {
+  unsigned int bar_count, bar_gen, abort, status;
+};
+
+
+// Grid-wide barrier of a cooperative launch, with a bounded wait: a block
+// that waits longer than kWaitLimitNs (or sees another block give up)
+// records a timeout and returns false so that the whole kernel exits.
+__device__ bool grid_barrier(BatchGlobal* g, unsigned int nblocks) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = &g->bar_gen;
+    volatile unsigned int* vab = &g->abort;
+    const unsigned int my = atomicAdd(&g->bar_gen, 0u);
+    __threadfence();
+    if (atomicAdd(&g->bar_count, 1u) == nblocks - 1) {
+      atomicExch(&g->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&g->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == my) {
+        if (*vab) { ok = 0; break; }
+        if (global_ns() - t0 > kWaitLimitNs) {
+          atomicExch(&g->abort, 1u);
+          atomicOr(&g->status, kStatusTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <typename T, int TX>
+__device__ __forceinline__ void load_tile_plain(T* tile, const T* __restrict__ in, const BatchInst& I, int np,
+                                                int x0) {
+  constexpr int HX = TX + 4;
+  for (int q = threadIdx.x; q < np * HX; q += TX) {
+    const int p = q / HX, c = q - p * HX, col = x0 + c;
+    tile[q] = col < I.px ? in[I.off + (long long)p * I.px + col] : T(0);
+  }
+}
+
+__device__ __forceinline__ Geo geo_of(const BatchInst& I, int bc) {
+  Geo g;
+  g.nx = I.nx;
+  g.ny = 1;
+  g.px = I.px;
+  g.rows = 1;
+  g.plane = I.px;
+  g.bcx = g.bcy = bc;
+  g.dx = I.dx;
+  g.dy = 1.0;
+  g.idx = I.idx;
+  g.idy = 1.0;
+  return g;
+}
+
+template <typename T, class PH, int TX>
+__global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict__ inst,
+                                                    const int2* __restrict__ tiles, int ntiles, int ninst,
+                                                    T* A, T* B, T* C, BatchCtl* ictl, BatchGlobal* g, const PH ph,
+                                                    int nsteps, double cfl, int oe_type, int bc, int init) {
+  constexpr int NC = PH::NC, NP = 2 * NC, HX = TX + 4;
+  __shared__ __align__(16) T tile[NP * HX];
+  __shared__ __align__(16) T faces[2 * (TX + 2) * NC + (TX + 2)];
+  __shared__ double red[64];
+  const unsigned int nb = gridDim.x;
+
+  if (init) {
+    // speeds at the cell averages of A -> first step size of every instance
+    for (int t = blockIdx.x; t < ntiles; t += nb) {
+      const int2 td = tiles[t];
+      const BatchInst I = inst[td.x];
+      double m = 0.0;
+      const int i = td.y + threadIdx.x;
+      if (i < I.nx) {
+        T u[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) u[c] = A[I.off + (long long)(c * 2) * I.px + G + i];
+        m = (double)ph.speed_x(u);
+      }
+      m = block_max<TX>(m, red);
+      if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, m);
+    }
+    if (!grid_barrier(g, nb)) return;
+    for (int i = blockIdx.x * TX + threadIdx.x; i < ninst; i += nb * TX) {
+      const double a = __longlong_as_double((long long)ictl[i].alpha_bits);
+      double dt = cfl * inst[i].dx / a;
+      if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; atomicOr(&g->status, kStatusNonFinite); }
+      ictl[i].dt = dt;
+      ictl[i].alpha_bits = 0ull;
+    }
+    if (!grid_barrier(g, nb)) return;
+  }
+
+  for (int s = 0; s < nsteps; ++s) {
+    for (int pass = 1; pass <= 4; ++pass) {
+      const T* in = pass == 1 ? A : pass == 2 ? B : pass == 3 ? C : B;
+      T* out = pass == 1 ? B : pass == 2 ? C : pass == 3 ? B : A;
+      for (int t = blockIdx.x; t < ntiles; t += nb) {
+        const int2 td = tiles[t];
+        const BatchInst I = inst[td.x];
+        const double dtd = ictl[td.x].dt;
+        if (!(dtd > 0.0)) continue;
+        __syncthreads();
+        load_tile_plain<T, TX>(tile, in, I, NP, td.y);
+        __syncthreads();
+        const Geo geo = geo_of(I, bc);
+        const T dt = T(dtd);
+        if (pass < 4) {
+          T* fL = faces;
+          T* fR = faces + (TX + 1) * NC;
+          const T* U0 = A + I.off;
+          T* Uo = out + I.off;
+          switch (I.k) {
+            case 3: stage1d_tile<T, 3, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
+            case 4: stage1d_tile<T, 4, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
+            case 5: stage1d_tile<T, 5, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
+            default: stage1d_tile<T, 6, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
+          }
+        } else {
+          T* tr = faces;
+          T* sp = faces + 2 * (TX + 2) * NC;
+          T* Uo = out + I.off;
+          const T gk = T(I.gamma_k);
+          double m;
+          switch (I.k) {
+            case 3: m = oe1d_tile<T, 3, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
+            case 4: m = oe1d_tile<T, 4, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
+            case 5: m = oe1d_tile<T, 5, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
+            default: m = oe1d_tile<T, 6, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
+          }
+          m = block_max<TX>(m, red);
+          if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, m);
+        }
+      }
+      if (!grid_barrier(g, nb)) return;
+    }
+    // per-instance clock and next step size
+    for (int i = blockIdx.x * TX + threadIdx.x; i < ninst; i += nb * TX) {
+      BatchCtl c = ictl[i];
+      if (c.dt > 0.0) {
+        c.t += c.dt;
+        c.steps += 1;
+        const double a = __longlong_as_double((long long)c.alpha_bits);
+        double dt = cfl * inst[i].dx / a;
+        if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; atomicOr(&g->status, kStatusNonFinite); }
+        c.dt = dt;
+      }
+      c.alpha_bits = 0ull;
+      ictl[i] = c;
+    }
+    if (!grid_barrier(g, nb)) return;
+  }
+}
+
+template <typename T, int TX>
+__global__ void fill_ghosts_batch(T* U, const BatchInst* inst, int ninst, int np, int bc) {
+  for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
+    const BatchInst I = inst[i];
+    Geo geo;
+    geo.nx = I.nx; geo.ny = 1; geo.px = I.px; geo.rows = 1; geo.plane = I.px; geo.bcx = geo.bcy = bc;
+    geo.dx = I.dx; geo.dy = 1.0; geo.idx = I.idx; geo.idy = 1.0;
+    for (int q = threadIdx.x; q < np * I.nx; q += blockDim.x) {
+      const int p = q / I.nx, c = q % I.nx;
+      const T v = U[I.off + (long long)p * I.px + G + c];
+      store_with_ghosts(U + I.off, geo, p, 0, c, v);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct fam_batch {
+  int n = 0, eq = FAM_EULER, bc = FAM_BC_OUTFLOW, prec = 64, nc = 3, np = 6;
+  double gamma = 1.4, ax = 1.0;
+  double gamma_k = 0.0;
+  int oe_type = 2;
+  size_t elem = 8;
+  std::vector<int> nx, k;
+  std::vector<BatchInst> hinst;
+  long long total = 0;  // elements per buffer
+  long long cells = 0;
+  BatchInst* dinst = nullptr;
+  int2* dtiles = nullptr;
+  int ntiles = 0;
+  int tile_x = 128;
+  int blocks_per_sm = 0;  // 0: occupancy maximum
+  int grid = 0;
+  void* buf[3] = {nullptr, nullptr, nullptr};
+  BatchCtl* ictl = nullptr;
+  BatchGlobal* glob = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool have_state = false, dt_valid = false;
+  double cfl_set = -1.0;
+  std::vector<std::pair<std::pair<long, double>, cudaGraphExec_t>> graphs;
+  std::string err;
+};
+
+static fam_status bfail(fam_batch* h, fam_status s, const std::string& m) {
+  if (h) h->err = m;
+  return s;
+}
+#define FAMB_CUDA(h, call)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return bfail(h, FAM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T, class PH, int TX>
+static cudaError_t launch_run(fam_batch* h, const PH& ph, long nsteps, double cfl, int init, bool query_only,
+                              int* grid_out) {
+  auto fn = batched1d_run<T, PH, TX>;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TX, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorLaunchOutOfResources;
+  int per_sm = h->blocks_per_sm > 0 ? std::min(h->blocks_per_sm, occ) : occ;
+  int grid = std::max(1, std::min(sms * per_sm, h->ntiles));
+  if (grid_out) *grid_out = grid;
+  if (query_only) return cudaSuccess;
+  T* A = reinterpret_cast<T*>(h->buf[0]);
+  T* B = reinterpret_cast<T*>(h->buf[1]);
+  T* C = reinterpret_cast<T*>(h->buf[2]);
+  int ntiles = h->ntiles, ninst = h->n, ns = (int)nsteps, oe = h->oe_type, bc = h->bc;
+  const BatchInst* di = h->dinst;
+  const int2* dtl = h->dtiles;
+  BatchCtl* ic = h->ictl;
+  BatchGlobal* gl = h->glob;
+  void* args[] = {(void*)&di, (void*)&dtl, (void*)&ntiles, (void*)&ninst, (void*)&A, (void*)&B, (void*)&C,
+                  (void*)&ic, (void*)&gl, (void*)&ph, (void*)&ns, (void*)&cfl, (void*)&oe, (void*)&bc,
+                  (void*)&init};
+  return cudaLaunchCooperativeKernel((void*)fn, dim3(grid), dim3(TX), args, 0, h->stream);
+}
+
+template <typename T, class PH>
+static cudaError_t launch_tx(fam_batch* h, const PH& ph, long nsteps, double cfl, int init, bool q, int* g) {
+  switch (h->tile_x) {
+    case 64: return launch_run<T, PH, 64>(h, ph, nsteps, cfl, init, q, g);
+    case 256: return launch_run<T, PH, 256>(h, ph, nsteps, cfl, init, q, g);
+    default: return launch_run<T, PH, 128>(h, ph, nsteps, cfl, init, q, g);
+  }
+}
+
+static cudaError_t launch(fam_batch* h, long nsteps, double cfl, int init, bool q = false, int* g = nullptr) {
+  const double gm = h->gamma;
+  if (h->prec == 64) {
+    switch (h->eq) {
+      case FAM_ADVECTION: return launch_tx<double>(h, Advection1D<double>{h->ax}, nsteps, cfl, init, q, g);
+      case FAM_BURGERS: return launch_tx<double>(h, Burgers1D<double>{}, nsteps, cfl, init, q, g);
+      default: return launch_tx<double>(h, Euler1D<double>{gm, gm - 1.0, 0.5 * (gm - 1.0)}, nsteps, cfl, init, q, g);
+    }
+  }
+  switch (h->eq) {
+    case FAM_ADVECTION: return launch_tx<float>(h, Advection1D<float>{(float)h->ax}, nsteps, cfl, init, q, g);
+    case FAM_BURGERS: return launch_tx<float>(h, Burgers1D<float>{}, nsteps, cfl, init, q, g);
+    default:
+      return launch_tx<float>(h, Euler1D<float>{(float)gm, (float)(gm - 1.0), (float)(0.5 * (gm - 1.0))}, nsteps,
+                              cfl, init, q, g);
+  }
+}
+
+static fam_status build_tiles(fam_batch* h) {
+  std::vector<int2> tl;
+  std::vector<int> order(h->n);
+  for (int i = 0; i < h->n; ++i) order[i] = i;
+  // costliest orders first so that every round of the block-cyclic walk has
+  // tiles of similar cost
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->k[a] > h->k[b]; });
+  for (int i : order)
+    for (int x0 = 0; x0 < h->nx[i]; x0 += h->tile_x) tl.push_back(make_int2(i, x0));
+  h->ntiles = (int)tl.size();
+  if (h->dtiles) cudaFree(h->dtiles);
+  h->dtiles = nullptr;
+  FAMB_CUDA(h, cudaMalloc(&h->dtiles, sizeof(int2) * tl.size()));
+  FAMB_CUDA(h, cudaMemcpy(h->dtiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  return FAM_OK;
+}
+
+static fam_status fill_ghosts(fam_batch* h, int b) {
+  if (h->prec == 64)
+    fill_ghosts_batch<double, 256><<<std::min(h->n, 4096), 256, 0, h->stream>>>(
+        reinterpret_cast<double*>(h->buf[b]), h->dinst, h->n, h->np, h->bc);
+  else
+    fill_ghosts_batch<float, 256><<<std::min(h->n, 4096), 256, 0, h->stream>>>(
+        reinterpret_cast<float*>(h->buf[b]), h->dinst, h->n, h->np, h->bc);
+  FAMB_CUDA(h, cudaGetLastError());
+  return FAM_OK;
+}
+
+static fam_status reset_clock(fam_batch* h) {
+  FAMB_CUDA(h, cudaMemsetAsync(h->ictl, 0, sizeof(BatchCtl) * h->n, h->stream));
+  FAMB_CUDA(h, cudaMemsetAsync(h->glob, 0, sizeof(BatchGlobal), h->stream));
+  return FAM_OK;
+}
+
+static fam_status ensure_init(fam_batch* h, double cfl) {
+  if (!h->have_state) return bfail(h, FAM_E_STATE, "no state");
+  if (!(cfl > 0.0)) return bfail(h, FAM_E_INVAL, "cfl must be positive");
+  if (h->dt_valid && cfl == h->cfl_set) return FAM_OK;
+  // step sizes from the current averages, no step
+  FAMB_CUDA(h, launch(h, 0, cfl, 1));
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->dt_valid = true;
+  h->cfl_set = cfl;
+  return FAM_OK;
+}
+
+extern "C" {
+
+fam_status fam_batch_create(fam_batch_t* out, int n_inst, const int* nx, const int* k, double x0, double x1,
+                            int equation, int bc, double gamma, int precision, void* stream) {
+  if (!out || !nx || !k || n_inst <= 0) return FAM_E_INVAL;
+  *out = nullptr;
+  if (equation < FAM_ADVECTION || equation > FAM_EULER) return FAM_E_INVAL;
+  if (bc != FAM_BC_PERIODIC && bc != FAM_BC_OUTFLOW) return FAM_E_INVAL;
+  if (precision != 64 && precision != 32) return FAM_E_INVAL;
+  if (!(x1 > x0)) return FAM_E_INVAL;
+  if (equation == FAM_EULER && !(gamma > 1.0)) return FAM_E_INVAL;
+  for (int i = 0; i < n_inst; ++i)
+    if (nx[i] < 4 || k[i] < 3 || k[i] > 6) return FAM_E_INVAL;
+  const char* fault = std::getenv("FAM_FAULT_ALLOC");
+  if (fault && fault[0] == '1') return FAM_E_NOMEM;
+  fam_batch* h = new fam_batch();
+  h->n = n_inst;
+  h->eq = equation;
+  h->bc = bc;
+  h->prec = precision;
+  h->gamma = gamma;
+  h->ax = equation == FAM_ADVECTION ? gamma : 1.0;
+  h->nc = equation == FAM_EULER ? 3 : 1;
+  h->np = 2 * h->nc;
+  h->elem = precision == 64 ? 8 : 4;
+  h->nx.assign(nx, nx + n_inst);
+  h->k.assign(k, k + n_inst);
+  long long off = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    BatchInst I{};
+    I.off = off;
+    I.nx = nx[i];
+    I.px = ((nx[i] + 2 * G) + 3) / 4 * 4;
+    I.k = k[i];
+    I.dx = (x1 - x0) / nx[i];
+    I.idx = 1.0 / I.dx;
+    I.gamma_k = k[i] <= 4 ? 25.0 : 12.5;
+    off += (long long)I.px * h->np;
+    h->cells += nx[i];
+    h->hinst.push_back(I);
+  }
+  h->total = off;
+  auto bail = [&](fam_status s) {
+    fam_batch_destroy(h);
+    return s;
+  };
+  if (stream) {
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(FAM_E_CUDA);
+    h->own_stream = true;
+  }
+  for (int b = 0; b < 3; ++b) {
+    if (cudaMalloc(&h->buf[b], h->total * h->elem) != cudaSuccess) return bail(FAM_E_NOMEM);
+    cudaMemsetAsync(h->buf[b], 0, h->total * h->elem, h->stream);
+  }
+  if (cudaMalloc(&h->dinst, sizeof(BatchInst) * n_inst) != cudaSuccess) return bail(FAM_E_NOMEM);
+  if (cudaMalloc(&h->ictl, sizeof(BatchCtl) * n_inst) != cudaSuccess) return bail(FAM_E_NOMEM);
+  if (cudaMalloc(&h->glob, sizeof(BatchGlobal)) != cudaSuccess) return bail(FAM_E_NOMEM);
+  if (cudaMemcpy(h->dinst, h->hinst.data(), sizeof(BatchInst) * n_inst, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(FAM_E_CUDA);
+  if (build_tiles(h) != FAM_OK) return bail(FAM_E_CUDA);
+  if (reset_clock(h) != FAM_OK) return bail(FAM_E_CUDA);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FAM_E_CUDA);
+  *out = h;
+  return FAM_OK;
+}
+
+void fam_batch_destroy(fam_batch_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (int b = 0; b < 3; ++b)
+    if (h->buf[b]) cudaFree(h->buf[b]);
+  if (h->dinst) cudaFree(h->dinst);
+  if (h->dtiles) cudaFree(h->dtiles);
+  if (h->ictl) cudaFree(h->ictl);
+  if (h->glob) cudaFree(h->glob);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* fam_batch_last_error(fam_batch_t h) { return h ? h->err.c_str() : "null handle"; }
+
+fam_status fam_batch_set_option(fam_batch_t h, const char* key, double v) {
+  if (!h || !key) return FAM_E_INVAL;
+  std::string k(key);
+  if (k == "oe_type") {
+    if (v != 0.0 && v != 2.0) return bfail(h, FAM_E_INVAL, "oe_type must be 0 or 2");
+    h->oe_type = (int)v;
+  } else if (k == "gamma_k") {
+    for (auto& I : h->hinst) I.gamma_k = v > 0.0 ? v : (I.k <= 4 ? 25.0 : 12.5);
+    FAMB_CUDA(h, cudaMemcpy(h->dinst, h->hinst.data(), sizeof(BatchInst) * h->n, cudaMemcpyHostToDevice));
+  } else if (k == "ax") {
+    h->ax = v;
+  } else if (k == "tile_x") {
+    if (v != 64.0 && v != 128.0 && v != 256.0) return bfail(h, FAM_E_INVAL, "tile_x must be 64, 128 or 256");
+    h->tile_x = (int)v;
+    return build_tiles(h);
+  } else if (k == "blocks_per_sm") {
+    h->blocks_per_sm = (int)v;
+  } else {
+    return bfail(h, FAM_E_INVAL, "unknown option " + k);
+  }
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->dt_valid = false;
+  return FAM_OK;
+}
+
+static fam_status batch_copy(fam_batch* h, void* dst_user, const void* src_user, int on_device, int b, bool in) {
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  long long uoff = 0;
+  for (int i = 0; i < h->n; ++i) {
+    const BatchInst& I = h->hinst[i];
+    const size_t row = (size_t)I.nx * h->elem;
+    char* dev = reinterpret_cast<char*>(h->buf[b]) + (size_t)(I.off + G) * h->elem;
+    if (in) {
+      const char* src = reinterpret_cast<const char*>(src_user) + uoff * h->elem;
+      FAMB_CUDA(h, cudaMemcpy2DAsync(dev, (size_t)I.px * h->elem, src, row, row, h->np, kind, h->stream));
+    } else {
+      char* dst = reinterpret_cast<char*>(dst_user) + uoff * h->elem;
+      FAMB_CUDA(h, cudaMemcpy2DAsync(dst, row, dev, (size_t)I.px * h->elem, row, h->np, kind, h->stream));
+    }
+    uoff += (long long)I.nx * h->np;
+  }
+  return FAM_OK;
+}
+
+fam_status fam_batch_set_state(fam_batch_t h, const void* U, int on_device) {
+  if (!h || !U) return FAM_E_INVAL;
+  fam_status s = batch_copy(h, nullptr, U, on_device, 0, true);
+  if (s) return s;
+  s = fill_ghosts(h, 0);
+  if (s) return s;
+  s = reset_clock(h);
+  if (s) return s;
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->have_state = true;
+  h->dt_valid = false;
+  return FAM_OK;
+}
+
+fam_status fam_batch_get_state(fam_batch_t h, void* U, int on_device) {
+  if (!h || !U) return FAM_E_INVAL;
+  if (!h->have_state) return bfail(h, FAM_E_STATE, "no state");
+  fam_status s = batch_copy(h, U, nullptr, on_device, 0, false);
+  if (s) return s;
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_batch_run(fam_batch_t h, long nsteps, double cfl) {
+  if (!h) return FAM_E_INVAL;
+  if (nsteps < 0) return bfail(h, FAM_E_INVAL, "nsteps < 0");
+  fam_status s = ensure_init(h, cfl);
+  if (s) return s;
+  if (nsteps == 0) return FAM_OK;
+  for (auto& kv : h->graphs)
+    if (kv.first.first == nsteps && kv.first.second == cfl) {
+      FAMB_CUDA(h, cudaGraphLaunch(kv.second, h->stream));
+      return FAM_OK;
+    }
+  // capture the persistent cooperative launch into a graph once per (nsteps, cfl)
+  cudaGraph_t graph;
+  FAMB_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = launch(h, nsteps, cfl, 0);
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    // capture of a cooperative launch not available: launch directly
+    if (ce == cudaSuccess) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    FAMB_CUDA(h, launch(h, nsteps, cfl, 0));
+    return FAM_OK;
+  }
+  cudaGraphExec_t exec;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    FAMB_CUDA(h, launch(h, nsteps, cfl, 0));
+    return FAM_OK;
+  }
+  h->graphs.push_back({{nsteps, cfl}, exec});
+  FAMB_CUDA(h, cudaGraphLaunch(exec, h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_batch_sync(fam_batch_t h) {
+  if (!h) return FAM_E_INVAL;
+  BatchGlobal g;
+  FAMB_CUDA(h, cudaMemcpyAsync(&g, h->glob, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (g.status & kStatusTimeout) return bfail(h, FAM_E_TIMEOUT, "grid barrier timed out");
+  if (g.status & (kStatusNonFinite | kStatusNonPhysical)) return bfail(h, FAM_E_NONPHYSICAL, "non-physical state");
+  return FAM_OK;
+}
+
+fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps) {
+  if (!h) return FAM_E_INVAL;
+  std::vector<BatchCtl> c(h->n);
+  FAMB_CUDA(h, cudaMemcpyAsync(c.data(), h->ictl, sizeof(BatchCtl) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->n; ++i) {
+    if (t) t[i] = c[i].t;
+    if (dt) dt[i] = c[i].dt;
+    if (steps) steps[i] = (long)c[i].steps;
+  }
+  return FAM_OK;
+}
+
+fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, long* cells) {
+  if (!h) return FAM_E_INVAL;
+  int g = 0;
+  FAMB_CUDA(h, launch(h, 0, 1.0, 0, true, &g));
+  if (tile_x) *tile_x = h->tile_x;
+  if (grid) *grid = g;
+  if (ntiles) *ntiles = h->ntiles;
+  if (cells) *cells = h->cells;
+  return FAM_OK;
+}
+
+fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char* cache_path, int* tile_x_out,
+                          int* blocks_per_sm_out) {
+  if (!h) return FAM_E_INVAL;
+  if (!h->have_state) return bfail(h, FAM_E_STATE, "no state");
+  if (probe_steps < 1) probe_steps = 1;
+  // key of this configuration
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  std::ostringstream key;
+  key << prop.name << "|eq" << h->eq << "|p" << h->prec << "|n" << h->n << "|cells" << h->cells;
+  if (cache_path && cache_path[0]) {
+    std::ifstream f(cache_path);
+    std::string line;
+    while (std::getline(f, line)) {
+      std::istringstream ls(line);
+      std::string k;
+      int tx = 0, bps = 0;
+      if (std::getline(ls, k, '\t') && (ls >> tx >> bps) && k == key.str()) {
+        h->tile_x = tx;
+        h->blocks_per_sm = bps;
+        fam_status s = build_tiles(h);
+        if (s) return s;
+        h->dt_valid = false;
+        if (tile_x_out) *tile_x_out = tx;
+        if (blocks_per_sm_out) *blocks_per_sm_out = bps;
+        return FAM_OK;
+      }
+    }
+  }
+  // save the state, time each candidate from the same state, restore
+  void* save = nullptr;
+  FAMB_CUDA(h, cudaMalloc(&save, h->total * h->elem));
+  FAMB_CUDA(h, cudaMemcpyAsync(save, h->buf[0], h->total * h->elem, cudaMemcpyDeviceToDevice, h->stream));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best_tx = h->tile_x, best_b = h->blocks_per_sm;
+  float best = 1e30f;
+  const int txs[3] = {64, 128, 256};
+  for (int tx : txs) {
+    h->tile_x = tx;
+    if (build_tiles(h) != FAM_OK) continue;
+    int occ_grid = 0;
+    h->blocks_per_sm = 0;
+    if (launch(h, 0, cfl, 0, true, &occ_grid) != cudaSuccess) continue;
+    for (int frac = 1; frac <= 2; ++frac) {
+      int dev_sms = prop.multiProcessorCount;
+      int occ = std::max(1, occ_grid / dev_sms);
+      int bps = frac == 1 ? occ : std::max(1, occ / 2);
+      if (frac == 2 && bps == occ) continue;
+      h->blocks_per_sm = bps;
+      cudaMemcpyAsync(h->buf[0], save, h->total * h->elem, cudaMemcpyDeviceToDevice, h->stream);
+      reset_clock(h);
+      if (launch(h, 0, cfl, 1) != cudaSuccess) { cudaGetLastError(); continue; }
+      cudaEventRecord(e0, h->stream);
+      cudaError_t le = launch(h, probe_steps, cfl, 0);
+      cudaEventRecord(e1, h->stream);
+      if (le != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) { cudaGetLastError(); continue; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_tx = tx;
+        best_b = bps;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tile_x = best_tx;
+  h->blocks_per_sm = best_b;
+  fam_status s = build_tiles(h);
+  FAMB_CUDA(h, cudaMemcpyAsync(h->buf[0], save, h->total * h->elem, cudaMemcpyDeviceToDevice, h->stream));
+  reset_clock(h);
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  cudaFree(save);
+  h->dt_valid = false;
+  if (s) return s;
+  if (cache_path && cache_path[0]) {
+    std::ofstream f(cache_path, std::ios::app);
+    f << key.str() << '\t' << best_tx << ' ' << best_b << '\n';
+  }
+  if (tile_x_out) *tile_x_out = best_tx;
+  if (blocks_per_sm_out) *blocks_per_sm_out = best_b;
+  return FAM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// fam_internal.cuh -- private host-side definitions shared by the C ABI
+// (fam_api.cu) and the per-configuration kernel instantiation units
+// (fam_inst.cu): the handle, the launch table and the launchers.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fam.h"
+#include "fam_kernels1d.cuh"
+
+using namespace fam;
+
+// tile shapes
+constexpr int TX2 = 32, TY2 = 8;   // 2D: 256 threads, one cell each
+constexpr int TX1 = 128;           // 1D: 128 cells per block
+
+// ---------------------------------------------------------------------------
+// per-configuration launchers
+// ---------------------------------------------------------------------------
+struct Ops {
+  cudaError_t (*stage)(struct fam_handle*, int in, int u0, int out, int stage);
+  cudaError_t (*oe)(struct fam_handle*, int in, int out, double dt_override);
+  cudaError_t (*alpha)(struct fam_handle*, int buf);
+  cudaError_t (*prepare)();  // set shared-memory attributes
+};
+
+struct fam_handle {
+  int d = 1, k = 5, eq = FAM_EULER, bc = FAM_BC_PERIODIC, prec = 64;
+  fam_grid grid{};
+  Geo geo{};
+  int nc = 1, nm = 2, np = 2;
+  double gamma = 1.4, ax = 1.0, ay = 1.0;
+  int oe_type = 2;
+  double gamma_k = 0.0;
+  int oe_q6 = 1;
+  int smooth_dt = 0;
+  double dt_max = 0.0;
+  size_t elem = 8;
+  size_t buf_elems = 0;
+  void* buf[3] = {nullptr, nullptr, nullptr};
+  FamCtl* ctl = nullptr;
+  CUtensorMap tm[3];
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool have_state = false;
+  bool dt_valid = false;
+  double cfl_set = -1.0;
+  double T_set = 0.0;
+  std::map<long, cudaGraphExec_t> graphs;
+  Ops ops{};
+  std::string err;
+  // opt-in per-kernel timing (option "profile"): 5 events per step bracket
+  // the three stage launches and the OE launch of fam_step()
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double prof_ms[4] = {0, 0, 0, 0};
+  long prof_steps = 0;
+};
+
+inline fam_status fail(fam_handle* h, fam_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+inline fam_status cuda_fail(fam_handle* h, cudaError_t e, const char* where) {
+  return fail(h, FAM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FAM_CUDA(h, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);  \
+  } while (0)
+
+template <typename T> inline T* bufp(fam_handle* h, int b) { return reinterpret_cast<T*>(h->buf[b]); }
+
+template <typename T, class PH> PH make_phys(const fam_handle* h);
+template <> inline Advection1D<double> make_phys<double, Advection1D<double>>(const fam_handle* h) { return {h->ax}; }
+template <> inline Advection1D<float> make_phys<float, Advection1D<float>>(const fam_handle* h) { return {(float)h->ax}; }
+template <> inline Burgers1D<double> make_phys<double, Burgers1D<double>>(const fam_handle*) { return {}; }
+template <> inline Burgers1D<float> make_phys<float, Burgers1D<float>>(const fam_handle*) { return {}; }
+template <> inline Euler1D<double> make_phys<double, Euler1D<double>>(const fam_handle* h) {
+  return {h->gamma, h->gamma - 1.0, 0.5 * (h->gamma - 1.0)};
+}
+template <> inline Euler1D<float> make_phys<float, Euler1D<float>>(const fam_handle* h) {
+  return {(float)h->gamma, (float)(h->gamma - 1.0), (float)(0.5 * (h->gamma - 1.0))};
+}
+template <> inline Advection2D<double> make_phys<double, Advection2D<double>>(const fam_handle* h) { return {h->ax, h->ay}; }
+template <> inline Advection2D<float> make_phys<float, Advection2D<float>>(const fam_handle* h) {
+  return {(float)h->ax, (float)h->ay};
+}
+template <> inline Burgers2D<double> make_phys<double, Burgers2D<double>>(const fam_handle*) { return {}; }
+template <> inline Burgers2D<float> make_phys<float, Burgers2D<float>>(const fam_handle*) { return {}; }
+template <> inline Euler2D<double> make_phys<double, Euler2D<double>>(const fam_handle* h) {
+  return {h->gamma, h->gamma - 1.0, 0.5 * (h->gamma - 1.0)};
+}
+template <> inline Euler2D<float> make_phys<float, Euler2D<float>>(const fam_handle* h) {
+  return {(float)h->gamma, (float)(h->gamma - 1.0), (float)(0.5 * (h->gamma - 1.0))};
+}
+
+inline double default_gamma_k(const fam_handle* h) {
+  if (h->gamma_k > 0.0) return h->gamma_k;
+  if (h->k <= 4) return 25.0;
+  return h->d == 1 ? 12.5 : 15.0;
+}
+
+template <typename T, int K, class PH>
+struct Impl2D {
+  using S = Smem2D<T, PH::NC, TX2, TY2>;
+  static cudaError_t prepare() {
+    cudaError_t e = cudaFuncSetAttribute(stage2d<T, K, PH, TX2, TY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::bytes_stage);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(oe2d<T, K, PH, TX2, TY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)S::bytes_oe);
+  }
+  static dim3 grid(const fam_handle* h) {
+    return dim3((h->geo.nx + TX2 - 1) / TX2, (h->geo.ny + TY2 - 1) / TY2);
+  }
+  static cudaError_t stage(fam_handle* h, int in, int u0, int out, int s) {
+    stage2d<T, K, PH, TX2, TY2><<<grid(h), TX2 * TY2, S::bytes_stage, h->stream>>>(
+        h->tm[in], bufp<T>(h, u0), bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
+    return cudaGetLastError();
+  }
+  static cudaError_t oe(fam_handle* h, int in, int out, double dto) {
+    oe2d<T, K, PH, TX2, TY2><<<grid(h), TX2 * TY2, S::bytes_oe, h->stream>>>(
+        h->tm[in], bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, h->oe_type, T(default_gamma_k(h)),
+        h->oe_q6, dto);
+    return cudaGetLastError();
+  }
+  static cudaError_t alpha(fam_handle* h, int b) {
+    long long n = (long long)h->geo.nx * h->geo.ny;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 8);
+    alpha2d<T, PH, 256><<<blocks, 256, 0, h->stream>>>(bufp<T>(h, b), h->geo, make_phys<T, PH>(h), h->ctl);
+    return cudaGetLastError();
+  }
+};
+
+template <typename T, int K, class PH>
+struct Impl1D {
+  using S = Smem1D<T, PH::NC, TX1>;
+  static cudaError_t prepare() {
+    cudaError_t e = cudaFuncSetAttribute(stage1d<T, K, PH, TX1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::bytes_stage);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(oe1d<T, K, PH, TX1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_oe);
+  }
+  static dim3 grid(const fam_handle* h) { return dim3((h->geo.nx + TX1 - 1) / TX1); }
+  static cudaError_t stage(fam_handle* h, int in, int u0, int out, int s) {
+    stage1d<T, K, PH, TX1><<<grid(h), TX1, S::bytes_stage, h->stream>>>(
+        h->tm[in], bufp<T>(h, u0), bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
+    return cudaGetLastError();
+  }
+  static cudaError_t oe(fam_handle* h, int in, int out, double dto) {
+    oe1d<T, K, PH, TX1><<<grid(h), TX1, S::bytes_oe, h->stream>>>(h->tm[in], bufp<T>(h, out), h->geo,
+                                                                   make_phys<T, PH>(h), h->ctl, h->oe_type,
+                                                                   T(default_gamma_k(h)), dto);
+    return cudaGetLastError();
+  }
+  static cudaError_t alpha(fam_handle* h, int b) {
+    int blocks = std::min((h->geo.nx + 255) / 256, 148 * 8);
+    alpha1d<T, PH, 256><<<blocks, 256, 0, h->stream>>>(bufp<T>(h, b), h->geo, make_phys<T, PH>(h), h->ctl);
+    return cudaGetLastError();
+  }
+};
+
+template <class I> Ops ops_of() { return Ops{&I::stage, &I::oe, &I::alpha, &I::prepare}; }
+
+// per-configuration selectors, one per instantiation unit (fam_inst.cu)
+#define FAM_DECL_PICK(D, P, K) bool fam_pick_d##D##_p##P##_k##K(fam_handle* h);
+#define FAM_DECL_PICK_K(D, P) FAM_DECL_PICK(D, P, 3) FAM_DECL_PICK(D, P, 4) FAM_DECL_PICK(D, P, 5) FAM_DECL_PICK(D, P, 6)
+FAM_DECL_PICK_K(1, 64)
+FAM_DECL_PICK_K(1, 32)
+FAM_DECL_PICK_K(2, 64)
+FAM_DECL_PICK_K(2, 32)
+#undef FAM_DECL_PICK_K
+#undef FAM_DECL_PICK

@@ -1,0 +1,475 @@
+// fam_kernels2d.cuh -- 2D FAM kernels (sm_103a).
+//
+//  stage2d  one SSP-RK3 stage (eq. 12): TMA-staged tile + halo of the
+//           structure-of-arrays moment planes, compact reconstruction of each
+//           cell (Sec. 2.4), Rusanov fluxes at the four Gauss points of every
+//           face, 4x4 Gauss volume terms, the residual of eq. (11), the
+//           Shu--Osher combination and the ghost layers of the output.
+//  oe2d     end-of-step OE (eq. 2dOE_sol / 2dOE_system, Tab. sigma2d) on the
+//           final stage; averages are copied unchanged.  Fused: the
+//           max Rusanov speeds at cell averages for the next time step.
+//  alpha2d  the same speed reduction alone (first step).
+//
+// Thread layout: one thread per cell of a TX x TY tile; the tile's
+// surrounding ring of cells computes only the face traces the tile needs.
+#pragma once
+
+#include "fam_phys.cuh"
+#include "fam_recon.cuh"
+
+namespace fam {
+
+template <typename T>
+struct Coefs2D {
+  T a0, a1, a2;  // Shu--Osher: out = a1 * U0 + a2 * (Us + dt R)   (a0 unused)
+};
+
+__device__ __forceinline__ void stage_weights(int stage, double& w0, double& w1) {
+  // out = w0 * U0 + w1 * (Us + dt R)
+  if (stage == 1) { w0 = 0.0; w1 = 1.0; }
+  else if (stage == 2) { w0 = 0.75; w1 = 0.25; }
+  else { w0 = 1.0 / 3.0; w1 = 2.0 / 3.0; }
+}
+
+// Write v to cell (i, j) of plane p and to every ghost image of that cell.
+template <typename T>
+__device__ __forceinline__ void store_with_ghosts(T* __restrict__ out, const Geo& g, int p, int j, int i, T v) {
+  int xs[3], ys[3];
+  int nxs = 0, nys = 0;
+  xs[nxs++] = i + G;
+  if (g.bcx == 0) {
+    if (i < G) xs[nxs++] = i + G + g.nx;
+    if (i >= g.nx - G) xs[nxs++] = i + G - g.nx;
+  } else {
+    if (i == 0) { xs[nxs++] = 0; xs[nxs++] = 1; }
+    if (i == g.nx - 1) { xs[nxs++] = g.nx + G; xs[nxs++] = g.nx + G + 1; }
+  }
+  if (g.rows > 1) {
+    ys[nys++] = j + G;
+    if (g.bcy == 0) {
+      if (j < G) ys[nys++] = j + G + g.ny;
+      if (j >= g.ny - G) ys[nys++] = j + G - g.ny;
+    } else {
+      if (j == 0) { ys[nys++] = 0; ys[nys++] = 1; }
+      if (j == g.ny - 1) { ys[nys++] = g.ny + G; ys[nys++] = g.ny + G + 1; }
+    }
+  } else {
+    ys[nys++] = 0;
+  }
+  T* base = out + (long long)p * g.plane;
+  for (int b = 0; b < nys; ++b)
+    for (int a = 0; a < nxs; ++a) base[(long long)ys[b] * g.px + xs[a]] = v;
+}
+
+// Shared-memory layout of the 2D kernels (in elements of T).
+template <typename T, int NC, int TX, int TY>
+struct Smem2D {
+  static constexpr int NP = NC * 3;
+  static constexpr int HX = TX + 4, HY = TY + 4;
+  static constexpr int TILE = NP * HY * HX;
+  static constexpr int XF = (TX + 1) * TY * 4 * NC;  // x-face slots
+  static constexpr int YF = TX * (TY + 1) * 4 * NC;  // y-face slots
+  static constexpr size_t bytes_stage = sizeof(T) * (size_t)(TILE + 2 * XF + 2 * YF) + 16 + 64 * sizeof(double);
+  static constexpr size_t bytes_oe =
+      sizeof(T) * (size_t)(TILE + 4 * NC * (TX + 2) * (TY + 2) + 2 * (TX + 2) * (TY + 2)) + 16 + 64 * sizeof(double);
+};
+
+// Issue the TMA load of the tile + halo (box (TX+4) x (TY+4) x NP planes at
+// padded coordinates (x0, y0, 0)) and wait for it.  Returns false on timeout.
+template <typename T, int NP, int HX, int HY>
+__device__ __forceinline__ bool load_tile(T* tile, uint64_t* bar, const CUtensorMap* tm, int x0, int y0,
+                                          FamCtl* ctl) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (uint32_t)(sizeof(T) * NP * HY * HX));
+    tma_load_3d(tile, tm, bar, x0, y0, 0);
+  }
+  bool ok = mbar_wait(bar, 0);
+  if (!ok) {
+    atomicOr(&ctl->status, kStatusTimeout);
+    mbar_wait(bar, 0);  // let an in-flight copy land before the block exits
+  }
+  return ok;
+}
+
+// Gather the 3x3 patch of moments of component c around tile position (hx, hy).
+template <typename T, int HX, int HY>
+__device__ __forceinline__ void gather_patch(const T* tile, int c, int hx, int hy, T* A, T* X, T* Y) {
+  const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX;
+  const T* px = tile + (size_t)(c * 3 + 1) * HY * HX;
+  const T* py = tile + (size_t)(c * 3 + 2) * HY * HX;
+#pragma unroll
+  for (int s = 0; s < 9; ++s) {
+    const int o = (hy + s / 3 - 1) * HX + (hx + s % 3 - 1);
+    A[s] = pa[o];
+    X[s] = px[o];
+    Y[s] = py[o];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage kernel
+// ---------------------------------------------------------------------------
+// stage = 1, 2, 3: Shu--Osher stage; stage = 0: write the residual R only.
+template <typename T, int K, class PH, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 1)
+    stage2d(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ U0, T* __restrict__ Uout,
+            const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
+  constexpr int NC = PH::NC;
+  using S = Smem2D<T, NC, TX, TY>;
+  constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
+  constexpr int D = K - 1;
+  constexpr int NCOEF = Recon2D<K>::NCOEF;
+  constexpr int NT = TX * TY;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* xL = tile + S::TILE;  // left-side trace of x-face, later the flux
+  T* xR = xL + S::XF;
+  T* yB = xR + S::XF;      // bottom-side trace of y-face, later the flux
+  T* yT = yB + S::YF;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(yT + S::YF);
+
+  const double dtd = (stage == 0) ? 0.0 : ctl->dt;
+  if (stage != 0 && !(dtd > 0.0)) return;  // run finished: keep the state
+  const T dt = T(dtd);
+
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  if (threadIdx.x == 0) prefetch_tmap(&tm_in);
+  if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int hx = tx + 2, hy = ty + 2;
+  const T wg[4] = {T(famgen::kGaussW[0]), T(famgen::kGaussW[1]), T(famgen::kGaussW[2]), T(famgen::kGaussW[3])};
+
+  // ---- phase A: reconstruction, volume terms, traces --------------------
+  T coef[NC][NCOEF];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T A[9], X[9], Y[9];
+    gather_patch<T, HX, HY>(tile, c, hx, hy, A, X, Y);
+    Recon2D<K>::coef(A, X, Y, coef[c]);
+  }
+  T VA[PH::NVA];
+#pragma unroll
+  for (int q = 0; q < PH::NVA; ++q) VA[q] = T(0);
+
+  // eta pairs: (+inner, -inner) -> Gauss nodes (2, 1); (+outer, -outer) -> (3, 0)
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    T up[NC][4], um[NC][4];  // values at the 4 xi nodes for eta = +node / -node
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T dp[D + 1], dm[D + 1];
+      if (pr == 0) eta_pair<T, D, kRowInner>(coef[c], dp, dm);
+      else eta_pair<T, D, kRowOuter>(coef[c], dp, dm);
+      const int hp = pr == 0 ? 2 : 3, hm = pr == 0 ? 1 : 0;
+      // volume values: xi nodes 2/1 (inner pair), 3/0 (outer pair); traces at xi = +/- 1/2
+      sym_pair<T, D, kRowInner>(dp, up[c][2], up[c][1]);
+      sym_pair<T, D, kRowOuter>(dp, up[c][3], up[c][0]);
+      sym_pair<T, D, kRowInner>(dm, um[c][2], um[c][1]);
+      sym_pair<T, D, kRowOuter>(dm, um[c][3], um[c][0]);
+      T rp, lp, rm, lm;
+      sym_pair<T, D, kRowHalf>(dp, rp, lp);
+      sym_pair<T, D, kRowHalf>(dm, rm, lm);
+      // this cell's right trace = left side of x-face tx+1; left trace = right side of face tx
+      xL[((ty * (TX + 1) + tx + 1) * 4 + hp) * NC + c] = rp;
+      xL[((ty * (TX + 1) + tx + 1) * 4 + hm) * NC + c] = rm;
+      xR[((ty * (TX + 1) + tx) * 4 + hp) * NC + c] = lp;
+      xR[((ty * (TX + 1) + tx) * 4 + hm) * NC + c] = lm;
+    }
+    const int hp = pr == 0 ? 2 : 3, hm = pr == 0 ? 1 : 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      T u[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) u[c] = up[c][g];
+      ph.vol_acc(u, wg[hp] * wg[g], VA);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) u[c] = um[c][g];
+      ph.vol_acc(u, wg[hm] * wg[g], VA);
+    }
+  }
+  // y-face traces: eta = +1/2 (top) and -1/2 (bottom) at the 4 xi nodes
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T dp[D + 1], dm[D + 1];
+    eta_pair<T, D, kRowHalf>(coef[c], dp, dm);
+    T t[4], b[4];
+    sym_pair<T, D, kRowInner>(dp, t[2], t[1]);
+    sym_pair<T, D, kRowOuter>(dp, t[3], t[0]);
+    sym_pair<T, D, kRowInner>(dm, b[2], b[1]);
+    sym_pair<T, D, kRowOuter>(dm, b[3], b[0]);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      yB[(((ty + 1) * TX + tx) * 4 + g) * NC + c] = t[g];
+      yT[((ty * TX + tx) * 4 + g) * NC + c] = b[g];
+    }
+  }
+  // ring cells around the tile: only the trace facing the tile
+  for (int r = threadIdx.x; r < 2 * (TX + TY); r += NT) {
+    int rx, ry, kind;
+    if (r < TY) { rx = -1; ry = r; kind = 0; }                          // left: right trace
+    else if (r < 2 * TY) { rx = TX; ry = r - TY; kind = 1; }            // right: left trace
+    else if (r < 2 * TY + TX) { rx = r - 2 * TY; ry = -1; kind = 2; }   // bottom: top trace
+    else { rx = r - 2 * TY - TX; ry = TY; kind = 3; }                   // top: bottom trace
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T A[9], X[9], Y[9], t[4];
+      gather_patch<T, HX, HY>(tile, c, rx + 2, ry + 2, A, X, Y);
+      if (kind == 0) {
+        Recon2D<K>::tr_xp(A, X, Y, t);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) xL[((ry * (TX + 1) + 0) * 4 + g) * NC + c] = t[g];
+      } else if (kind == 1) {
+        Recon2D<K>::tr_xm(A, X, Y, t);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) xR[((ry * (TX + 1) + TX) * 4 + g) * NC + c] = t[g];
+      } else if (kind == 2) {
+        Recon2D<K>::tr_yp(A, X, Y, t);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) yB[((0 * TX + rx) * 4 + g) * NC + c] = t[g];
+      } else {
+        Recon2D<K>::tr_ym(A, X, Y, t);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) yT[((TY * TX + rx) * 4 + g) * NC + c] = t[g];
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- phase B: Rusanov fluxes at every face Gauss point -----------------
+  constexpr int NXP = (TX + 1) * TY * 4, NYP = TX * (TY + 1) * 4;
+  for (int it = threadIdx.x; it < NXP + NYP; it += NT) {
+    T uL[NC], uR[NC], fL[NC], fR[NC];
+    T* slot;
+    const T* other;
+    T sL, sR;
+    if (it < NXP) {
+      slot = xL + it * NC;
+      other = xR + it * NC;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { uL[c] = slot[c]; uR[c] = other[c]; }
+      sL = ph.flux_x(uL, fL);
+      sR = ph.flux_x(uR, fR);
+    } else {
+      slot = yB + (it - NXP) * NC;
+      other = yT + (it - NXP) * NC;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { uL[c] = slot[c]; uR[c] = other[c]; }
+      sL = ph.flux_y(uL, fL);
+      sR = ph.flux_y(uR, fR);
+    }
+    const T a = fmax(sL, sR);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) slot[c] = T(0.5) * (fL[c] + fR[c]) - T(0.5) * a * (uR[c] - uL[c]);
+  }
+  __syncthreads();
+
+  // ---- phase C: residual (eq. 11), Shu--Osher combination, store ---------
+  const int i = x0 + tx, j = y0 + ty;
+  if (i >= geo.nx || j >= geo.ny) return;
+  const T idx_ = T(geo.idx), idy_ = T(geo.idy);
+  T avg[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) avg[c] = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
+  T V1[NC], V2[NC];
+  ph.vol_finish(VA, avg, V1, V2);
+  double w0, w1;
+  stage_weights(stage, w0, w1);
+  const T gx[4] = {T(famgen::kGaussX[0]), T(famgen::kGaussX[1]), T(famgen::kGaussX[2]), T(famgen::kGaussX[3])};
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const T* fl = xL + ((ty * (TX + 1) + tx) * 4) * NC + c;
+    const T* fr = xL + ((ty * (TX + 1) + tx + 1) * 4) * NC + c;
+    const T* fb = yB + ((ty * TX + tx) * 4) * NC + c;
+    const T* ft = yB + (((ty + 1) * TX + tx) * 4) * NC + c;
+    T sxl = T(0), sxr = T(0), syb = T(0), syt = T(0), mx = T(0), my = T(0);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const T a = fl[g * NC], b = fr[g * NC], cb = fb[g * NC], ct = ft[g * NC];
+      sxl = fma(wg[g], a, sxl);
+      sxr = fma(wg[g], b, sxr);
+      syb = fma(wg[g], cb, syb);
+      syt = fma(wg[g], ct, syt);
+      mx = fma(wg[g] * gx[g], b - a, mx);   // int eta (f_x(+1/2) - f_x(-1/2)) over the x-faces
+      my = fma(wg[g] * gx[g], ct - cb, my);
+    }
+    T R[3];
+    R[0] = -(sxr - sxl) * idx_ - (syt - syb) * idy_;
+    R[1] = (V1[c] - T(0.5) * (sxr + sxl)) * idx_ - my * idy_;
+    R[2] = (V2[c] - T(0.5) * (syt + syb)) * idy_ - mx * idx_;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int p = c * 3 + m;
+      T v;
+      if (stage == 0) {
+        v = R[m];
+      } else {
+        const T us = tile[(size_t)p * HY * HX + hy * HX + hx];
+        if (stage == 1) {
+          v = us + dt * R[m];
+        } else {
+          const T u0 = U0[cell_index(geo, p, j, i)];
+          v = T(w0) * u0 + T(w1) * (us + dt * R[m]);
+        }
+      }
+      store_with_ghosts(Uout, geo, p, j, i, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// OE kernel (+ wave-speed reduction for the next step)
+// ---------------------------------------------------------------------------
+template <typename T, int K, class PH, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 1)
+    oe2d(const __grid_constant__ CUtensorMap tm_in, T* __restrict__ Uout, const Geo geo, const PH ph,
+         FamCtl* __restrict__ ctl, const int oe_type, const T gamma_k, const int q6, const double dt_override) {
+  constexpr int NC = PH::NC;
+  using S = Smem2D<T, NC, TX, TY>;
+  constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
+  constexpr int NT = TX * TY;
+  constexpr int RX = TX + 2, RY = TY + 2;  // tile plus one ring
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* fc = tile + S::TILE;            // face-centre traces [RY][RX][4][NC]
+  T* sp = fc + 4 * NC * RX * RY;     // speeds at averages [2][RY][RX]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sp + 2 * RX * RY);
+  double* red = reinterpret_cast<double*>(bar + 2);
+
+  const double dtd = dt_override >= 0.0 ? dt_override : ctl->dt;
+  const bool reduce = dt_override < 0.0;
+  if (!(dtd > 0.0) && reduce) return;
+  const T dt = T(dtd);
+
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  if (threadIdx.x == 0) prefetch_tmap(&tm_in);
+  if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
+
+  // traces at face centres and speeds at averages for the tile and its ring
+  for (int q = threadIdx.x; q < RX * RY; q += NT) {
+    const int rx = q % RX, ry = q / RX;  // ring coordinates: cell (x0 + rx - 1, y0 + ry - 1)
+    const int hx = rx + 1, hy = ry + 1;
+    const bool corner = (rx == 0 || rx == RX - 1) && (ry == 0 || ry == RY - 1);
+    T u[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      u[c] = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
+      if (!corner) {
+        T A[9], X[9], Y[9], t[4];
+        gather_patch<T, HX, HY>(tile, c, hx, hy, A, X, Y);
+        Recon2D<K>::facec(A, X, Y, t, q6);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) fc[(q * 4 + f) * NC + c] = t[f];
+      }
+    }
+    T sx, sy;
+    ph.speeds(u, sx, sy);
+    sp[q] = sx;
+    sp[RX * RY + q] = sy;
+  }
+  __syncthreads();
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool inside = i < geo.nx && j < geo.ny;
+  double my_speed_x = 0.0, my_speed_y = 0.0;
+  if (inside) {
+    const int rx = tx + 1, ry = ty + 1, q = ry * RX + rx;
+    const int hx = tx + 2, hy = ty + 2;
+    T sig_x = T(0), sig_y = T(0);
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      // jumps [[u]] = u(right/top side) - u(left/bottom side) at the four face centres
+      const T jxl = fc[(q * 4 + 0) * NC + c] - fc[((q - 1) * 4 + 1) * NC + c];
+      const T jxr = fc[((q + 1) * 4 + 0) * NC + c] - fc[(q * 4 + 1) * NC + c];
+      const T jyb = fc[(q * 4 + 2) * NC + c] - fc[((q - RX) * 4 + 3) * NC + c];
+      const T jyt = fc[((q + RX) * 4 + 2) * NC + c] - fc[(q * 4 + 3) * NC + c];
+      const T* pa = tile + (size_t)(c * 3) * HY * HX;
+      T v[9], S = T(0), mabs = T(0);
+#pragma unroll
+      for (int s = 0; s < 9; ++s) {
+        v[s] = pa[(hy + s / 3 - 1) * HX + (hx + s % 3 - 1)];
+        S += v[s];
+        mabs = fmax(mabs, fabs(v[s]));
+      }
+      T Dn = T(0);
+#pragma unroll
+      for (int s = 0; s < 9; ++s) Dn = fmax(Dn, fabs(v[s] - S));
+      const T eps = T(1e-14) * fmax(mabs, T(1));
+      if (oe_type != 0 && !(Dn < eps)) {
+        const T g = gamma_k * Fast<T>::rcp(Dn);
+        sig_x = fmax(sig_x, g * (fabs(jxl) + fabs(jxr)));
+        sig_y = fmax(sig_y, g * (fabs(jyb) + fabs(jyt)));
+      }
+    }
+    T bx = T(0), by = T(0);
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+      const int qq = (ry + s / 3 - 1) * RX + (rx + s % 3 - 1);
+      bx = fmax(bx, sp[qq]);
+      by = fmax(by, sp[RX * RY + qq]);
+    }
+    const T theta = bx * dt * sig_x * T(geo.idx) + by * dt * sig_y * T(geo.idy);
+    const T delta = Fast<T>::exp_(-theta);
+    T uavg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T a = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
+      uavg[c] = a;
+      const T m1 = tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx] * delta;
+      const T m2 = tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx] * delta;
+      if (!isfinite(a) || !isfinite(m1) || !isfinite(m2)) ok = false;
+      store_with_ghosts(Uout, geo, c * 3 + 0, j, i, a);
+      store_with_ghosts(Uout, geo, c * 3 + 1, j, i, m1);
+      store_with_ghosts(Uout, geo, c * 3 + 2, j, i, m2);
+    }
+    if (!ok) atomicOr(&ctl->status, kStatusNonFinite);
+    else if (!ph.admissible(uavg)) atomicOr(&ctl->status, kStatusNonPhysical);
+    my_speed_x = (double)sp[q];
+    my_speed_y = (double)sp[RX * RY + q];
+  }
+  if (!reduce) return;
+  const double mx = block_max<NT>(my_speed_x, red);
+  const double my = block_max<NT>(my_speed_y, red + 32);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&ctl->alpha_bits[0], mx);
+    atomic_max_nonneg(&ctl->alpha_bits[1], my);
+    step_epilogue(ctl, gridDim.x * gridDim.y, true);
+  }
+}
+
+// Max Rusanov speeds at cell averages -> ctl->dt (no time advance).
+template <typename T, class PH, int NT>
+__global__ void __launch_bounds__(NT) alpha2d(const T* __restrict__ U, const Geo geo, const PH ph,
+                                              FamCtl* __restrict__ ctl) {
+  __shared__ double red[64];
+  double mx = 0.0, my = 0.0;
+  const long long n = (long long)geo.nx * geo.ny;
+  for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < n; q += (long long)gridDim.x * NT) {
+    const int i = (int)(q % geo.nx), j = (int)(q / geo.nx);
+    T u[PH::NC];
+#pragma unroll
+    for (int c = 0; c < PH::NC; ++c) u[c] = U[cell_index(geo, c * 3, j, i)];
+    T sx, sy;
+    ph.speeds(u, sx, sy);
+    mx = fmax(mx, (double)sx);
+    my = fmax(my, (double)sy);
+  }
+  mx = block_max<NT>(mx, red);
+  my = block_max<NT>(my, red + 32);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&ctl->alpha_bits[0], mx);
+    atomic_max_nonneg(&ctl->alpha_bits[1], my);
+    step_epilogue(ctl, gridDim.x, false);
+  }
+}
+
+}  // namespace fam

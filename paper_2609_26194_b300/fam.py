@@ -1,0 +1,343 @@
+"""Thin ctypes binding of the FAM C ABI (include/fam.h).
+
+Argument marshalling only: every step of the FAM time step runs in the CUDA
+kernels of libfam.so.  The library must have been built
+(``python -m paper_2609_26194_b300.build``); loading fails loudly otherwise.
+
+States are numpy arrays (host) or torch CUDA tensors (device) in the layout
+U[c, m, j, i] (1D: U[c, m, i]); float64 for precision 64, float32 for 32.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfam.so")
+
+ADVECTION, BURGERS, EULER = 0, 1, 2
+PERIODIC, OUTFLOW = 0, 1
+STATUS = {0: "FAM_OK", 1: "FAM_E_INVAL", 2: "FAM_E_NOMEM", 3: "FAM_E_CUDA", 4: "FAM_E_NONPHYSICAL",
+          5: "FAM_E_TIMEOUT", 6: "FAM_E_STATE", 7: "FAM_E_UNSUPPORTED"}
+
+# every function declared in include/fam.h
+EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fam_step", "fam_run_steps",
+           "fam_run", "fam_sync", "fam_time", "fam_profile", "fam_residual", "fam_oe", "fam_last_error",
+           "fam_status_string", "fam_destroy", "fam_alu_peak", "fam_selftest_math",
+           "fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
+           "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
+           "fam_batch_last_error", "fam_batch_destroy")
+
+
+class FamError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfam.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FileNotFoundError(f"{LIB_PATH} missing: build it with `python -m paper_2609_26194_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, i, d, l = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_long
+        L.fam_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Grid), i, i, i, d, i, vp]
+        L.fam_set_option.argtypes = [vp, ctypes.c_char_p, d]
+        L.fam_set_state.argtypes = [vp, vp, i]
+        L.fam_get_state.argtypes = [vp, vp, i]
+        L.fam_step.argtypes = [vp, d]
+        L.fam_run_steps.argtypes = [vp, l, d]
+        L.fam_run.argtypes = [vp, d, d, l, ctypes.POINTER(l)]
+        L.fam_sync.argtypes = [vp]
+        L.fam_time.argtypes = [vp, dp, dp, ctypes.POINTER(l)]
+        L.fam_profile.argtypes = [vp, dp, ctypes.POINTER(l)]
+        L.fam_residual.argtypes = [vp, vp, vp, i]
+        L.fam_oe.argtypes = [vp, d, vp, vp, i]
+        L.fam_last_error.argtypes = [vp]
+        L.fam_last_error.restype = ctypes.c_char_p
+        L.fam_status_string.argtypes = [i]
+        L.fam_status_string.restype = ctypes.c_char_p
+        L.fam_destroy.argtypes = [vp]
+        L.fam_destroy.restype = None
+        L.fam_alu_peak.argtypes = [i, dp]
+        L.fam_selftest_math.argtypes = [dp, i, dp, dp, dp]
+        for name in EXPORTS:
+            if name not in ("fam_last_error", "fam_status_string", "fam_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One FAM problem on the GPU (wraps a fam_t handle)."""
+
+    def __init__(self, d: int, nx: int, ny: int = 1, box=(0.0, 1.0, 0.0, 1.0), k: int = 5,
+                 equation: int = EULER, bc: int = PERIODIC, gamma: float = 1.4, precision: int = 64,
+                 stream: int | None = None, **options):
+        self.d, self.nx, self.ny, self.k = d, nx, (ny if d == 2 else 1), k
+        self.equation, self.precision = equation, precision
+        self.ncomp = d + 2 if equation == EULER else 1
+        self.nmom = d + 1
+        self.dtype = np.float64 if precision == 64 else np.float32
+        g = Grid(d, nx, self.ny, box[0], box[1], box[2], box[3])
+        h = ctypes.c_void_p()
+        rc = lib().fam_create(ctypes.byref(h), ctypes.byref(g), k, equation, bc, gamma, precision,
+                              ctypes.c_void_p(stream or 0))
+        if rc != 0:
+            raise FamError(rc, "fam_create failed")
+        self._h = h
+        for key, val in options.items():
+            self.set_option(key, val)
+
+    @property
+    def shape(self) -> tuple:
+        if self.d == 1:
+            return (self.ncomp, self.nmom, self.nx)
+        return (self.ncomp, self.nmom, self.ny, self.nx)
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise FamError(rc, lib().fam_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fam_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_option(self, key: str, value: float):
+        self._check(lib().fam_set_option(self._h, key.encode(), float(value)))
+
+    def _buf(self, U):
+        if _is_torch(U):
+            if tuple(U.shape) != self.shape or not U.is_contiguous():
+                raise ValueError(f"tensor must be contiguous with shape {self.shape}")
+            want = "torch.float64" if self.precision == 64 else "torch.float32"
+            if str(U.dtype) != want:
+                raise TypeError(f"tensor dtype must be {want}")
+            return ctypes.c_void_p(U.data_ptr()), (1 if U.is_cuda else 0), U
+        A = np.ascontiguousarray(U, dtype=self.dtype)
+        if A.shape != self.shape:
+            raise ValueError(f"array shape {A.shape} != {self.shape}")
+        return ctypes.c_void_p(A.ctypes.data), 0, A
+
+    def set_state(self, U):
+        p, dev, keep = self._buf(U)
+        self._check(lib().fam_set_state(self._h, p, dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        p, dev, keep = self._buf(out)
+        self._check(lib().fam_get_state(self._h, p, dev))
+        return out
+
+    def step(self, cfl: float):
+        self._check(lib().fam_step(self._h, float(cfl)))
+
+    def run_steps(self, nsteps: int, cfl: float):
+        self._check(lib().fam_run_steps(self._h, int(nsteps), float(cfl)))
+
+    def run(self, T: float, cfl: float, max_steps: int = 0) -> int:
+        n = ctypes.c_long()
+        self._check(lib().fam_run(self._h, float(T), float(cfl), int(max_steps), ctypes.byref(n)))
+        return n.value
+
+    def sync(self):
+        self._check(lib().fam_sync(self._h))
+
+    def time(self) -> tuple[float, float, int]:
+        t, dt, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_long()
+        self._check(lib().fam_time(self._h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(s)))
+        return t.value, dt.value, s.value
+
+    def profile(self) -> tuple[list, int]:
+        """(ms per kernel [stage1, stage2, stage3, oe], profiled steps)."""
+        ms = (ctypes.c_double * 4)()
+        n = ctypes.c_long()
+        self._check(lib().fam_profile(self._h, ms, ctypes.byref(n)))
+        return list(ms), n.value
+
+    def residual(self, U):
+        p, dev, keep = self._buf(U)
+        out = np.empty(self.shape, dtype=self.dtype) if not dev else keep.new_empty(self.shape)
+        q, dev2, keep2 = self._buf(out)
+        self._check(lib().fam_residual(self._h, p, q, dev))
+        return out
+
+    def oe(self, dt: float, U):
+        p, dev, keep = self._buf(U)
+        out = np.empty(self.shape, dtype=self.dtype) if not dev else keep.new_empty(self.shape)
+        q, dev2, keep2 = self._buf(out)
+        self._check(lib().fam_oe(self._h, float(dt), p, q, dev))
+        return out
+
+
+def alu_peak(precision: int = 64) -> float:
+    v = ctypes.c_double()
+    rc = lib().fam_alu_peak(precision, ctypes.byref(v))
+    if rc != 0:
+        raise FamError(rc, "fam_alu_peak failed")
+    return v.value
+
+
+def selftest_math(x: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    outs = [np.empty_like(x) for _ in range(3)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().fam_selftest_math(x.ctypes.data_as(dp), x.size, *(o.ctypes.data_as(dp) for o in outs))
+    if rc != 0:
+        raise FamError(rc, "fam_selftest_math failed")
+    return tuple(outs)
+
+
+class Batch:
+    """Many independent 1D problems advanced in one persistent launch (fam_batch_t)."""
+
+    def __init__(self, nx, k, x0: float = 0.0, x1: float = 1.0, equation: int = EULER, bc: int = OUTFLOW,
+                 gamma: float = 1.4, precision: int = 64, stream: int | None = None):
+        self.nx = [int(v) for v in nx]
+        self.k = [int(v) for v in k]
+        if len(self.nx) != len(self.k):
+            raise ValueError("nx and k must have the same length")
+        self.n = len(self.nx)
+        self.ncomp = 3 if equation == EULER else 1
+        self.precision = precision
+        self.dtype = np.float64 if precision == 64 else np.float32
+        L = lib()
+        _batch_sigs(L)
+        h = ctypes.c_void_p()
+        anx = (ctypes.c_int * self.n)(*self.nx)
+        ak = (ctypes.c_int * self.n)(*self.k)
+        rc = L.fam_batch_create(ctypes.byref(h), self.n, anx, ak, x0, x1, equation, bc, gamma, precision,
+                                ctypes.c_void_p(stream or 0))
+        if rc != 0:
+            raise FamError(rc, "fam_batch_create failed")
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise FamError(rc, lib().fam_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fam_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key: str, value: float):
+        self._check(lib().fam_batch_set_option(self._h, key.encode(), float(value)))
+
+    def pack(self, states) -> np.ndarray:
+        parts = []
+        for U, n in zip(states, self.nx):
+            U = np.ascontiguousarray(U, dtype=self.dtype)
+            if U.shape != (self.ncomp, 2, n):
+                raise ValueError(f"instance state shape {U.shape} != {(self.ncomp, 2, n)}")
+            parts.append(U.reshape(-1))
+        return np.ascontiguousarray(np.concatenate(parts))
+
+    def unpack(self, flat) -> list:
+        out, o = [], 0
+        for n in self.nx:
+            m = self.ncomp * 2 * n
+            out.append(flat[o:o + m].reshape(self.ncomp, 2, n))
+            o += m
+        return out
+
+    def set_state(self, states):
+        flat = self.pack(states)
+        self._check(lib().fam_batch_set_state(self._h, ctypes.c_void_p(flat.ctypes.data), 0))
+
+    def get_state(self) -> list:
+        flat = np.empty(sum(self.ncomp * 2 * n for n in self.nx), dtype=self.dtype)
+        self._check(lib().fam_batch_get_state(self._h, ctypes.c_void_p(flat.ctypes.data), 0))
+        return self.unpack(flat)
+
+    def run(self, nsteps: int, cfl: float):
+        self._check(lib().fam_batch_run(self._h, int(nsteps), float(cfl)))
+
+    def sync(self):
+        self._check(lib().fam_batch_sync(self._h))
+
+    def times(self):
+        t = np.empty(self.n)
+        dt = np.empty(self.n)
+        st = (ctypes.c_long * self.n)()
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(lib().fam_batch_times(self._h, t.ctypes.data_as(dp), dt.ctypes.data_as(dp), st))
+        return t, dt, np.array(st[:], dtype=np.int64)
+
+    def info(self) -> dict:
+        tx, g, nt, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_long(), ctypes.c_long()
+        self._check(lib().fam_batch_info(self._h, ctypes.byref(tx), ctypes.byref(g), ctypes.byref(nt),
+                                         ctypes.byref(nc)))
+        return {"tile_x": tx.value, "grid": g.value, "tiles": nt.value, "cells": nc.value}
+
+    def tune(self, cfl: float, probe_steps: int = 3, cache_path: str | None = None) -> tuple[int, int]:
+        tx, b = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().fam_batch_tune(self._h, float(cfl), int(probe_steps),
+                                         cache_path.encode() if cache_path else None, ctypes.byref(tx),
+                                         ctypes.byref(b)))
+        return tx.value, b.value
+
+
+_batch_ready = False
+
+
+def _batch_sigs(L):
+    global _batch_ready
+    if _batch_ready:
+        return
+    vp, dp, i, d, l = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_long
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.fam_batch_create.argtypes = [ctypes.POINTER(vp), i, ip, ip, d, d, i, i, d, i, vp]
+    L.fam_batch_set_option.argtypes = [vp, ctypes.c_char_p, d]
+    L.fam_batch_set_state.argtypes = [vp, vp, i]
+    L.fam_batch_get_state.argtypes = [vp, vp, i]
+    L.fam_batch_run.argtypes = [vp, l, d]
+    L.fam_batch_sync.argtypes = [vp]
+    L.fam_batch_times.argtypes = [vp, dp, dp, ctypes.POINTER(l)]
+    L.fam_batch_info.argtypes = [vp, ip, ip, ctypes.POINTER(l), ctypes.POINTER(l)]
+    L.fam_batch_tune.argtypes = [vp, d, i, ctypes.c_char_p, ip, ip]
+    L.fam_batch_last_error.argtypes = [vp]
+    L.fam_batch_last_error.restype = ctypes.c_char_p
+    L.fam_batch_destroy.argtypes = [vp]
+    L.fam_batch_destroy.restype = None
+    for name in ("fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
+                 "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune"):
+        getattr(L, name).restype = ctypes.c_int
+    _batch_ready = True

@@ -152,17 +152,22 @@ def euler2d_smooth(n: int = 4096, gamma: float = GAMMA, box=(0.0, 1.0, 0.0, 1.0)
     return np.ascontiguousarray(np.stack([rho, u * rho, v * rho, E]))
 
 
-def euler2d_rectangles(n: int = 4096, seed: int = 3, nrect: int = 64,
-                       gamma: float = GAMMA) -> np.ndarray:
-    """Piecewise-constant periodic rectangles painted in order (moments vanish)."""
+def euler2d_rectangles(n: int = 4096, seed: int = 3, nrect: int = 64, gamma: float = GAMMA,
+                       lo: float = 0.1, hi: float = 5.0, vmax: float = 1.0) -> np.ndarray:
+    """Piecewise-constant periodic rectangles painted in order (moments vanish).
+
+    rho, p ~ U[lo, hi], u, v ~ U[-vmax, vmax].  The default ranges are the
+    shock-run recipe; without a positivity limiter the scheme admits only
+    milder contrasts (``ADMISSIBLE_RECT`` = rho, p in [0.5, 2.5], |u|,|v| <= 0.5).
+    """
     rng = np.random.default_rng(seed)
     prim = np.empty((4, n, n))
     prim[0], prim[1], prim[2], prim[3] = 1.0, 0.0, 0.0, 1.0
-    lo, hi = max(1, n // 32), max(2, n // 4)
+    wmin, wmax = max(1, n // 32), max(2, n // 4)
     for _ in range(nrect):
         i0, j0 = rng.integers(0, n, 2)
-        wx, wy = rng.integers(lo, hi + 1, 2)
-        st = (rng.uniform(0.1, 5.0), rng.uniform(-1.0, 1.0), rng.uniform(-1.0, 1.0), rng.uniform(0.1, 5.0))
+        wx, wy = rng.integers(wmin, wmax + 1, 2)
+        st = (rng.uniform(lo, hi), rng.uniform(-vmax, vmax), rng.uniform(-vmax, vmax), rng.uniform(lo, hi))
         ii = (i0 + np.arange(wx)) % n
         jj = (j0 + np.arange(wy)) % n
         for c in range(4):
@@ -171,6 +176,9 @@ def euler2d_rectangles(n: int = 4096, seed: int = 3, nrect: int = 64,
     U = np.zeros((4, 3, n, n))
     U[:, 0] = cons
     return U
+
+
+ADMISSIBLE_RECT = dict(lo=0.5, hi=2.5, vmax=0.5)
 
 
 def euler2d_fourier(n: int = 1024, seed: int = 5, nmodes: int = 16, amp: float = 0.05,

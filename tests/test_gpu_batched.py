@@ -1,0 +1,102 @@
+"""Batched persistent 1D path (fam_batch_*) on the GPU.
+
+Each instance must evolve exactly (bit for bit) as the single-problem path
+does, match the FP64 oracle at the parity bar, take its own step size, and
+conserve its averages on periodic grids.  The autotuner must not change
+results."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_26194_b300 import fam, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(seed=0, n_inst=14):
+    rng = np.random.default_rng(seed)
+    nx = [int(v) for v in np.rint(np.exp(rng.uniform(np.log(40), np.log(900), n_inst)))]
+    ks = [3, 4, 5, 6] * (n_inst // 4) + [5] * (n_inst % 4)
+    states = []
+    for i, n in enumerate(nx):
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        amp = rng.uniform(0.05, 0.2)
+        f = lambda x, ph=ph, amp=amp: inputs.primitive_to_conservative_1d(
+            1 + amp * np.sin(2 * np.pi * x + ph[0]), 0.2 + amp * np.cos(2 * np.pi * x + ph[1]),
+            1 + amp * np.sin(4 * np.pi * x + ph[2]))
+        states.append(inputs.project_1d(f, n, 0.0, 1.0))
+    return nx, ks, states
+
+
+def _comp_err(a, b):
+    nc = b.shape[0]
+    A, B = a.reshape(nc, -1), b.reshape(nc, -1)
+    return float(np.max(np.max(np.abs(A - B), axis=1) / np.max(np.abs(B), axis=1)))
+
+
+@pytest.mark.parametrize("bc", [fam.OUTFLOW, fam.PERIODIC])
+def test_batch_matches_single_problem_bitwise_and_oracle(bc):
+    nx, ks, states = _instances(1)
+    b = fam.Batch(nx, ks, bc=bc)
+    b.set_state(states)
+    b.run(30, 0.3)
+    b.sync()
+    got = b.get_state()
+    t, dt, steps = b.times()
+    assert np.all(steps == 30)
+    assert len(set(np.round(dt, 15))) > 1  # instances take their own step sizes
+    obc = oracle.OUTFLOW if bc == fam.OUTFLOW else oracle.PERIODIC
+    for i, (n, k, U) in enumerate(zip(nx, ks, states)):
+        with fam.Solver(1, n, k=k, equation=fam.EULER, bc=bc) as s:
+            s.set_state(U)
+            s.run_steps(30, 0.3)
+            single = s.get_state()
+            ts, _, _ = s.time()
+        assert np.array_equal(got[i], single), i
+        assert ts == t[i]
+        if i % 3 == 0:
+            P = oracle.Problem(d=1, nx=n, k=k, eq=oracle.EULER, bc=(obc,) * 4)
+            want, tw, _ = oracle.run(P, U, nsteps=30, cfl=0.3)
+            assert _comp_err(got[i], want) < 1e-12
+            assert abs(tw - t[i]) < 1e-13
+        if bc == fam.PERIODIC:
+            for c in range(3):
+                assert abs(got[i][c, 0].sum() - U[c, 0].sum()) < 1e-12 * abs(U[c, 0].sum())
+
+
+def test_batch_riemann_instances_and_tuner():
+    rng = np.random.default_rng(4)
+    nx = [int(v) for v in np.rint(np.exp(rng.uniform(np.log(64), np.log(2000), 24)))]
+    ks = [int(v) for v in rng.integers(4, 7, 24)]
+    states = [inputs.euler1d_riemann(n, seed=40 + i) for i, n in enumerate(nx)]
+    b = fam.Batch(nx, ks, bc=fam.OUTFLOW)
+    b.set_state(states)
+    b.run(20, 0.3)
+    b.sync()
+    ref = b.get_state()
+    tx, bps = b.tune(0.3, probe_steps=2)
+    assert tx in (64, 128, 256) and bps >= 1
+    b.set_state(states)
+    b.run(20, 0.3)
+    b.sync()
+    again = b.get_state()
+    for r, a in zip(ref, again):
+        assert np.array_equal(r, a)
+    for i in (0, 7, 13):
+        P = oracle.Problem(d=1, nx=nx[i], k=ks[i], eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4)
+        want, _, _ = oracle.run(P, states[i], nsteps=20, cfl=0.3)
+        assert _comp_err(again[i], want) < 1e-12
+    info = b.info()
+    assert info["tile_x"] == tx and info["cells"] == sum(nx)
+
+
+def test_batch_reports_nonphysical_state():
+    nx, ks, states = _instances(2, n_inst=4)
+    states[2] = states[2].copy()
+    states[2][0, 0, 5] = -1.0
+    b = fam.Batch(nx, ks)
+    b.set_state(states)
+    b.run(2, 0.3)
+    with pytest.raises(fam.FamError) as e:
+        b.sync()
+    assert e.value.code == 4

@@ -1,0 +1,348 @@
+"""GPU parity of the CUDA FAM path against the FP64 CPU oracle, through the C ABI.
+
+Bar (FP64): relative max-norm per conserved component, max over the
+component's average and moment planes of |gpu - oracle| divided by the
+component's max |oracle|, below 1e-12.  The first moments are small
+differences of O(1) quantities (a moment is O(dx) and its residual is
+O(dx) while the flux terms that form it are O(1/dx)), so two correct FP64
+evaluations in different operation orders agree on them only to about
+1e-16 / dx^2 of their own size; each moment plane is therefore also held to
+a per-plane relative bar of 1e-9, which any error in a formula would exceed
+by orders of magnitude.  Sizes span several tiles with ragged tails (1D:
+128-cell tiles; 2D: 32 x 8 tiles).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_26194_b300 import fam, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+PLANE_TOL64 = 1e-9
+EQ = {"euler": (fam.EULER, oracle.EULER), "adv": (fam.ADVECTION, oracle.ADVECTION),
+      "burgers": (fam.BURGERS, oracle.BURGERS)}
+BC = {"periodic": (fam.PERIODIC, oracle.PERIODIC), "outflow": (fam.OUTFLOW, oracle.OUTFLOW)}
+
+
+def comp_err(a, b):
+    """max over components c of max|a_c - b_c| / max|b_c| (all planes of c)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nc = b.shape[0]
+    A, B = a.reshape(nc, -1), b.reshape(nc, -1)
+    return float(np.max(np.max(np.abs(A - B), axis=1) / np.max(np.abs(B), axis=1)))
+
+
+def plane_err(a, b):
+    """max over planes (c, m) of max|a - b| / max|b| on that plane."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nc, nm = b.shape[:2]
+    A, B = a.reshape(nc * nm, -1), b.reshape(nc * nm, -1)
+    floor = 1e-12 * np.max(np.abs(B))
+    errs = np.max(np.abs(A - B), axis=1) / np.maximum(np.max(np.abs(B), axis=1), floor)
+    return float(np.max(errs))
+
+
+def assert_parity(a, b, tol=TOL64, plane_tol=PLANE_TOL64):
+    ce, pe = comp_err(a, b), plane_err(a, b)
+    assert ce < tol and pe < plane_tol, (ce, pe)
+
+
+def make(d, n, k, eq="euler", bc="periodic", prec=64, box=None, **opt):
+    box = box or (0.0, 1.0, 0.0, 1.0)
+    if d == 1:
+        nx, ny = n, 1
+    else:
+        nx, ny = n
+    # the gamma argument of fam_create is the advection speed for FAM_ADVECTION
+    gamma = 1.0 if eq == "adv" else 1.4
+    solver = fam.Solver(d, nx, ny, box=box, k=k, equation=EQ[eq][0], bc=BC[bc][0], gamma=gamma, precision=prec,
+                        **opt)
+    P = oracle.Problem(d=d, nx=nx, ny=ny, x0=box[0], x1=box[1], y0=box[2], y1=box[3], k=k, eq=EQ[eq][1],
+                       bc=(BC[bc][1],) * 4, oe_type=int(opt.get("oe_type", 2)),
+                       gamma_k=float(opt.get("gamma_k", 0.0)), oe_jump_q6=int(opt.get("oe_jump_q6", 1)))
+    return solver, P
+
+
+def smooth_state(d, n, seed=0, amp=0.1):
+    """Smooth random-mode Euler state (positive density and pressure)."""
+    rng = np.random.default_rng(seed)
+    if d == 1:
+        ph = rng.uniform(0, 2 * np.pi, 6)
+        f = lambda x: inputs.primitive_to_conservative_1d(
+            1 + amp * np.sin(2 * np.pi * x + ph[0]) + 0.5 * amp * np.cos(6 * np.pi * x + ph[1]),
+            0.3 + amp * np.sin(4 * np.pi * x + ph[2]),
+            1 + amp * np.cos(2 * np.pi * x + ph[3]))
+        return inputs.project_1d(f, n, 0.0, 1.0)
+    nx, ny = n
+    ph = rng.uniform(0, 2 * np.pi, 8)
+    f = lambda X, Y: inputs.primitive_to_conservative_2d(
+        1 + amp * np.sin(2 * np.pi * (X + 2 * Y) + ph[0]),
+        0.3 + amp * np.cos(2 * np.pi * X + ph[1]),
+        -0.2 + amp * np.sin(4 * np.pi * Y + ph[2]),
+        1 + amp * np.cos(2 * np.pi * (X - Y) + ph[3]))
+    return inputs.project_2d(f, nx, ny)
+
+
+# ----------------------------------------------------------------------------
+# building blocks
+# ----------------------------------------------------------------------------
+
+def test_newton_reciprocal_and_sqrt_within_few_ulp():
+    rng = np.random.default_rng(5)
+    x = np.exp(rng.uniform(np.log(1e-6), np.log(1e6), 200000))
+    r, rs, sq = fam.selftest_math(x)
+    assert np.max(np.abs(r * x - 1.0)) < 4 * 2.2e-16
+    assert np.max(np.abs(rs / (1.0 / np.sqrt(x)) - 1.0)) < 4 * 2.2e-16
+    assert np.max(np.abs(sq / np.sqrt(x) - 1.0)) < 4 * 2.2e-16
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("eq,bc", [("euler", "periodic"), ("euler", "outflow"), ("adv", "periodic"),
+                                   ("burgers", "outflow")])
+def test_residual_1d(k, eq, bc):
+    n = 300
+    s, P = make(1, n, k, eq, bc)
+    U = smooth_state(1, n) if eq == "euler" else inputs.project_1d(
+        lambda x: (0.7 + 0.5 * np.sin(2 * np.pi * x) + 0.1 * np.cos(10 * np.pi * x))[None], n, 0.0, 1.0)
+    assert_parity(s.residual(U), oracle.residual(P, U))
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("eq,bc", [("euler", "periodic"), ("euler", "outflow"), ("adv", "periodic"),
+                                   ("burgers", "periodic")])
+def test_residual_2d(k, eq, bc):
+    n = (70, 45)
+    s, P = make(2, n, k, eq, bc, ax=1.0, ay=-0.6) if eq == "adv" else make(2, n, k, eq, bc)
+    if eq == "adv":
+        P.ax, P.ay = 1.0, -0.6
+    U = smooth_state(2, n) if eq == "euler" else inputs.project_2d(
+        lambda X, Y: (0.7 + 0.5 * np.sin(2 * np.pi * (X + Y)) + 0.1 * np.cos(6 * np.pi * X))[None], *n)
+    assert_parity(s.residual(U), oracle.residual(P, U))
+
+
+@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_oe_operator(d, k):
+    n = 300 if d == 1 else (70, 45)
+    s, P = make(d, n, k, "euler", "periodic")
+    U = smooth_state(d, n, seed=3, amp=0.25)
+    # rough moments so that the OE actually damps
+    rng = np.random.default_rng(7)
+    U[:, 1:] += 0.02 * rng.standard_normal(U[:, 1:].shape)
+    dt = 0.7 / (n if d == 1 else n[0])
+    got = s.oe(dt, U)
+    want, theta = oracle.oe(P, dt, U)
+    assert np.max(theta) > 1e-3
+    assert np.array_equal(got[:, 0], U[:, 0])  # averages exact
+    assert_parity(got, want)
+
+
+def test_oe_k6_p6_reading_option():
+    n = (40, 24)
+    s, P = make(2, n, 6, "euler", "periodic", oe_jump_q6=0)
+    U = smooth_state(2, n, seed=4, amp=0.25)
+    U[:, 1:] += 0.02 * np.random.default_rng(1).standard_normal(U[:, 1:].shape)
+    assert_parity(s.oe(0.01, U), oracle.oe(P, 0.01, U)[0])
+
+
+# ----------------------------------------------------------------------------
+# whole steps
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_100_steps_1d_euler(k, bc):
+    n = 300
+    s, P = make(1, n, k, "euler", bc)
+    U = smooth_state(1, n, seed=11, amp=0.2)
+    s.set_state(U)
+    s.run_steps(100, 0.3)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=100, cfl=0.3)
+    assert_parity(s.get_state(), want)
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_100_steps_1d_riemann(k):
+    """Discontinuous data (8 face-snapped jumps), outflow."""
+    n = 300
+    s, P = make(1, n, k, "euler", "outflow")
+    U = inputs.euler1d_riemann(n, seed=7)
+    s.set_state(U)
+    s.run_steps(100, 0.3)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=100, cfl=0.3)
+    assert_parity(s.get_state(), want)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_100_steps_2d_euler_smooth(k):
+    n = (70, 45)
+    s, P = make(2, n, k, "euler", "periodic")
+    U = smooth_state(2, n, seed=12, amp=0.2)
+    s.set_state(U)
+    s.run_steps(100, 0.4)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=100, cfl=0.4)
+    assert_parity(s.get_state(), want)
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_40_steps_2d_rectangles_outflow(k):
+    n = (72, 40)
+    s, P = make(2, n, k, "euler", "outflow")
+    U = inputs.euler2d_rectangles(72, seed=3, nrect=24, **inputs.ADMISSIBLE_RECT)[:, :, :40, :]
+    U = np.ascontiguousarray(U)
+    s.set_state(U)
+    s.run_steps(40, 0.4)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=40, cfl=0.4)
+    assert_parity(s.get_state(), want)
+
+
+def test_config1_advection_sine_to_T():
+    """1D advection, N = 200, k = 3, CFL 0.2 to T = 1, Type-II OE every step."""
+    s, P = make(1, 200, 3, "adv", "periodic")
+    U = inputs.advection_sine(200)
+    s.set_state(U)
+    n = s.run(1.0, 0.2)
+    t, dt, steps = s.time()
+    want, tw, nw = oracle.run(P, U, T=1.0, cfl=0.2)
+    assert t == 1.0 and n == nw
+    assert_parity(s.get_state(), want)
+
+
+def test_smooth_dt_rule_to_T():
+    s, P = make(1, 40, 5, "euler", "periodic", box=(0.0, 2.0, 0, 1), smooth_dt=1)
+    P.x1 = 2.0
+    U = inputs.euler1d_smooth(40)
+    s.set_state(U)
+    s.run(0.25, 0.1)
+    want, _, _ = oracle.run(P, U, T=0.25, cfl=0.1, smooth=True)
+    assert_parity(s.get_state(), want)
+
+
+def test_config2_full_size_100_steps_fp64_and_fp32_error():
+    """1D Euler N = 65536, k = 5, outflow, CFL 0.3 (FP64 parity; FP32 error stated)."""
+    n = 65536
+    U = inputs.euler1d_riemann(n, seed=2)
+    s, P = make(1, n, 5, "euler", "outflow")
+    s.set_state(U)
+    s.run_steps(100, 0.3)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=100, cfl=0.3)
+    assert_parity(s.get_state(), want)
+    s32, _ = make(1, n, 5, "euler", "outflow", prec=32)
+    s32.set_state(U.astype(np.float32))
+    s32.run_steps(100, 0.3)
+    s32.sync()
+    e32 = np.max(np.abs(s32.get_state()[:, 0] - want[:, 0])) / np.max(np.abs(want[:, 0]))
+    assert e32 < 1e-4, e32
+
+
+def _window_step(P_full, U, dt, j, i, R=10):
+    """Oracle one step on a (2R+1)^2 periodic window centred at (j, i)."""
+    ny, nx = U.shape[2:]
+    jj = (j + np.arange(-R, R + 1)) % ny
+    ii = (i + np.arange(-R, R + 1)) % nx
+    W = np.ascontiguousarray(U[:, :, jj][:, :, :, ii])
+    dx = (P_full.x1 - P_full.x0) / nx
+    dy = (P_full.y1 - P_full.y0) / ny
+    Pw = oracle.Problem(**{**P_full.__dict__, "nx": 2 * R + 1, "ny": 2 * R + 1, "x0": 0.0,
+                           "x1": dx * (2 * R + 1), "y0": 0.0, "y1": dy * (2 * R + 1)})
+    return oracle.step(Pw, W, dt)[:, :, R, R]
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_config3_full_size_sampled_one_step(k):
+    """2D Euler 4096^2 periodic: one step of the full grid on the GPU; the
+    oracle recomputes sampled cells on windows (radius 10 > 3 stages x 2 + OE 2)."""
+    n = 4096
+    U = inputs.euler2d_smooth(n)
+    cfl = 0.4 if k == 4 else 0.55
+    s, P = make(2, (n, n), k, "euler", "periodic")
+    s.set_state(U)
+    s.step(cfl)
+    s.sync()
+    V = s.get_state()
+    dt = oracle.dt(P, U, cfl)
+    rng = np.random.default_rng(k)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (5, 2047)] + [tuple(rng.integers(0, n, 2)) for _ in range(8)]
+    comp_scale = np.abs(U.reshape(4, -1)).max(axis=1)          # per conserved component
+    plane_scale = np.abs(U.reshape(12, -1)).max(axis=1).reshape(4, 3)
+    for j, i in pts:
+        want = _window_step(P, U, dt, j, i)
+        got = V[:, :, j, i]
+        diff = np.abs(got - want)
+        assert np.max(diff / comp_scale[:, None]) < TOL64, (j, i, diff)
+        assert np.max(diff / plane_scale) < PLANE_TOL64, (j, i, diff)
+    # conservation of every component's total on the periodic grid
+    for c in range(4):
+        s0, s1 = U[c, 0].sum(), V[c, 0].sum()
+        assert abs(s1 - s0) < 1e-11 * abs(s0)
+
+
+# ----------------------------------------------------------------------------
+# invariants, determinism, checkpoint / resume, error paths
+# ----------------------------------------------------------------------------
+
+def test_deterministic_and_checkpoint_resume_bitwise():
+    n = (96, 40)
+    U = smooth_state(2, n, seed=21, amp=0.2)
+    a, _ = make(2, n, 5, "euler", "periodic")
+    a.set_state(U)
+    a.run_steps(20, 0.5)
+    ref = a.get_state()
+    b, _ = make(2, n, 5, "euler", "periodic")
+    b.set_state(U)
+    b.run_steps(20, 0.5)
+    assert np.array_equal(b.get_state(), ref)
+    c, _ = make(2, n, 5, "euler", "periodic")
+    c.set_state(U)
+    c.run_steps(10, 0.5)
+    mid = c.get_state()
+    c.set_state(mid)
+    for _ in range(10):
+        c.step(0.5)
+    assert np.array_equal(c.get_state(), ref)
+
+
+def test_free_stream_is_preserved():
+    n = (40, 24)
+    U = np.zeros((4, 3, 24, 40))
+    U[:, 0] = inputs.primitive_to_conservative_2d(*(np.full((24, 40), v) for v in (1.3, 0.4, -0.2, 2.0)))
+    s, _ = make(2, n, 6, "euler", "outflow")
+    s.set_state(U)
+    s.run_steps(5, 0.5)
+    assert np.max(np.abs(s.get_state() - U)) < 1e-14
+
+
+def test_nonphysical_state_is_reported():
+    n = 256
+    U = smooth_state(1, n)
+    U[0, 0, 100] = -0.5
+    s, _ = make(1, n, 5, "euler", "periodic")
+    s.set_state(U)
+    s.step(0.3)
+    with pytest.raises(fam.FamError) as e:
+        s.sync()
+    assert e.value.code == 4
+
+
+def test_device_tensor_state_roundtrip():
+    torch = pytest.importorskip("torch")
+    n = (64, 32)
+    U = smooth_state(2, n, seed=2)
+    s, P = make(2, n, 4, "euler", "periodic")
+    t = torch.from_numpy(U).cuda()
+    s.set_state(t)
+    s.run_steps(3, 0.4)
+    out = torch.empty_like(t)
+    s.get_state(out)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=3, cfl=0.4)
+    assert_parity(out.cpu().numpy(), want)
