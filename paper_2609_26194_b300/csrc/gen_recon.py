@@ -309,9 +309,32 @@ def gen():
             fullpoly = sum(full[key] * LEG[key[0]] * LEG[key[1]].subs(XI, ETA) for key in full)
             assert sp.expand(fullpoly - Qs) == 0
             variants.append(("q", fullpoly))
+        # transpose of the coefficient map: cotangents of the 27 patch inputs
+        cb = sp.symbols(f"cb0:{len(keys)}")
+        cmap = {c: f"CB[{i}]" for i, c in enumerate(cb)}
+        inputs_ = list(a) + list(mx) + list(my)
+        forms = [sp.expand(coef[key]) for key in keys]
+        tforms = [sum(f.coeff(inp) * cbi for f, cbi in zip(forms, cb)) for inp in inputs_]
+        out.append(f"// 2D FAM{k}: transpose of fam2d_coef_k{k}: g[0..8] = avg, g[9..17] = x-moment,")
+        out.append("// g[18..26] = y-moment cotangents of the 3x3 patch from the coefficient cotangents CB")
+        out.append("template <typename T>")
+        out.append(f"__device__ __forceinline__ void fam2d_coefT_k{k}(const T* CB, T* g) {{")
+        out += emit_linear("g", tforms, cmap, prefix="s")
+        out.append("}")
+        out.append("")
         for tag, poly in variants:
             tr = [poly.subs({XI: -HALF, ETA: 0}), poly.subs({XI: HALF, ETA: 0}),
                   poly.subs({XI: 0, ETA: -HALF}), poly.subs({XI: 0, ETA: HALF})]
+            tb = sp.symbols("tb0:4")
+            tmap = {c: f"TB[{i}]" for i, c in enumerate(tb)}
+            trf = [sp.expand(e) for e in tr]
+            ttf = [sum(f.coeff(inp) * tbi for f, tbi in zip(trf, tb)) for inp in inputs_]
+            out.append(f"// 2D FAM{k}: transpose of fam2d_facec_k{k}{tag} (patch cotangents g[27] from TB[4])")
+            out.append("template <typename T>")
+            out.append(f"__device__ __forceinline__ void fam2d_facecT_k{k}{tag}(const T* TB, T* g) {{")
+            out += emit_linear("g", ttf, tmap, prefix="s")
+            out.append("}")
+            out.append("")
             out.append(f"// 2D FAM{k}: face-centre traces of {'p_' + str(k) if tag == 'p' else 'the full auxiliary Q6'}")
             out.append("// t[0] = u(-1/2,0), t[1] = u(1/2,0), t[2] = u(0,-1/2), t[3] = u(0,1/2)")
             out.append("template <typename T>")
