@@ -186,6 +186,36 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
 const char* fam_batch_last_error(fam_batch_t h);
 void fam_batch_destroy(fam_batch_t h);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free step (the paper has no counterpart: this is a calling
+ * convention for callers that cannot allocate device memory -- host
+ * applications that own a fixed device-memory budget and do not let plug-ins
+ * call cudaMalloc, and latency-critical loops where an allocation's cost and
+ * failure mode are not acceptable).
+ *
+ * One time step (three SSP-RK3 stages and the OE, as fam_step) of a 1D
+ * problem of nx <= FAM_NOALLOC_MAX_CELLS cells, from U_in to U_out, both
+ * caller-owned device buffers in the state layout of this header (element
+ * type per precision).  equation, bc, gamma, k, precision as in fam_create;
+ * the step size follows the CFL rule from U_in.  No device memory is
+ * allocated or freed: the intermediate states and the control block live in
+ * one static device array of the library (sized for FAM_NOALLOC_MAX_CELLS
+ * cells of 6 planes in FP64, about 2.4 MB), present on every GPU that loads
+ * the library until the process exits.  The first call on a device looks up
+ * that array's device address (once per device, with the device current), so
+ * make the first call on each device before any stream capture.  Every call
+ * reuses the same array: calls whose GPU work may overlap (other streams or
+ * host threads) race and must be serialised by the caller.  stream: a
+ * cudaStream_t or NULL for the legacy default stream.  If dt_used is not
+ * NULL the call synchronises the stream, writes the step size taken and
+ * reports FAM_E_NONPHYSICAL / FAM_E_TIMEOUT from the device flags;
+ * otherwise it is asynchronous.  Errors: FAM_E_INVAL (including nx above the
+ * limit), FAM_E_CUDA.
+ * ------------------------------------------------------------------------ */
+#define FAM_NOALLOC_MAX_CELLS 16384
+fam_status fam_step1d_noalloc(const void* U_in, void* U_out, int nx, double x0, double x1, int k, int equation,
+                              int bc, double gamma, int precision, double cfl, double* dt_used, void* stream);
+
 /* Measured throughput of this GPU's FP64 (precision 64) or FP32 (32) fused
  * multiply-add pipe in FLOP/s, from a register-resident FMA loop timed with
  * CUDA events (a roofline denominator; not part of the method). */

@@ -37,7 +37,8 @@ def nvcc() -> str:
 def units():
     out = [("fam_api", os.path.join(CSRC, "fam_api.cu"), []),
            ("fam_probe", os.path.join(CSRC, "fam_probe.cu"), []),
-           ("fam_batch", os.path.join(CSRC, "fam_batch.cu"), [])]
+           ("fam_batch", os.path.join(CSRC, "fam_batch.cu"), []),
+           ("fam_noalloc", os.path.join(CSRC, "fam_noalloc.cu"), [])]
     for d in (1, 2):
         for p in (64, 32):
             for k in (3, 4, 5, 6):

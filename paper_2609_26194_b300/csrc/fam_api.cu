@@ -100,6 +100,11 @@ static fam_status encode_maps(fam_handle* h) {
   return FAM_OK;
 }
 
+// shared with fam_noalloc.cu
+fam_status fam_internal_encode_maps(fam_handle* h) { return encode_maps(h); }
+fam_status fam_internal_fill_ghosts(fam_handle* h, int b) { return fill_ghosts(h, b); }
+bool fam_internal_pick(fam_handle* h) { return pick(h); }
+
 // ---------------------------------------------------------------------------
 // control block
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_status_string", "fam_destroy", "fam_alu_peak", "fam_selftest_math",
            "fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
            "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
-           "fam_batch_last_error", "fam_batch_destroy")
+           "fam_batch_last_error", "fam_batch_destroy", "fam_step1d_noalloc")
 
 
 class FamError(RuntimeError):
@@ -341,3 +341,29 @@ def _batch_sigs(L):
                  "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune"):
         getattr(L, name).restype = ctypes.c_int
     _batch_ready = True
+
+
+def step1d_noalloc(U_in, U_out, nx: int, k: int, x0: float = 0.0, x1: float = 1.0, equation: int = EULER,
+                   bc: int = PERIODIC, gamma: float = 1.4, cfl: float = 0.3, stream: int | None = None,
+                   return_dt: bool = True) -> float | None:
+    """One 1D time step from U_in to U_out (contiguous CUDA tensors of shape
+    (ncomp, 2, nx), float64 or float32) without any device allocation by the
+    library: its intermediate states live in a fixed static device array
+    (at most FAM_NOALLOC_MAX_CELLS = 16384 cells).  Calls share that array,
+    so calls whose GPU work may overlap must be serialised by the caller."""
+    L = lib()
+    _noalloc_sig(L)
+    prec = 64 if str(U_in.dtype) == "torch.float64" else 32
+    dt = ctypes.c_double()
+    rc = L.fam_step1d_noalloc(ctypes.c_void_p(U_in.data_ptr()), ctypes.c_void_p(U_out.data_ptr()), int(nx),
+                              float(x0), float(x1), int(k), int(equation), int(bc), float(gamma), prec, float(cfl),
+                              ctypes.byref(dt) if return_dt else None, ctypes.c_void_p(stream or 0))
+    if rc != 0:
+        raise FamError(rc, "fam_step1d_noalloc failed")
+    return dt.value if return_dt else None
+
+
+def _noalloc_sig(L):
+    vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    L.fam_step1d_noalloc.argtypes = [vp, vp, i, d, d, i, i, i, d, i, d, ctypes.POINTER(d), vp]
+    L.fam_step1d_noalloc.restype = ctypes.c_int
