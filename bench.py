@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--cfl", type=float, default=None)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain report")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-plain report")
+    ap.add_argument("--batched-steps", type=int, default=500)
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -189,6 +193,115 @@ def run_reference(a):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """Max of a per-rank scalar over all ranks (the timed region's length)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, cells: int, steps: int, ms: float) -> float:
+    """Whole-job cell-stage updates/s of `world` independent replicas, each
+    advancing `cells` cells by `steps` steps of 3 stages, over the max time."""
+    return world * 3.0 * cells * steps / (ms * 1e-3)
+
+
+def batched_report(a, torch):
+    """Many independent 1D Euler problems (4096 instances, N log-uniform in
+    [64, 16384], k uniform in {3..6}, outflow, CFL 0.3, Riemann data), 500
+    steps in one persistent launch, against the plain per-instance step loop."""
+    from paper_2609_26194_b300 import fam, inputs
+    insts = inputs.batched_1d(4096, seed=4)
+    nx = [U.shape[-1] for _, U in insts]
+    ks = [k for k, _ in insts]
+    cells = sum(nx)
+    b = fam.Batch(nx, ks, bc=fam.OUTFLOW)
+    b.set_state([U for _, U in insts])
+    tx, bps = b.tune(0.3, probe_steps=2)
+    b.set_state([U for _, U in insts])
+    b.run(0, 0.3)
+    b.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(a.batched_steps, 0.3)
+    status = "ok"
+    try:
+        b.sync()
+    except fam.FamError as e:  # a non-physical instance: timing stands, flag it
+        status = str(e)
+    batched_s = time.perf_counter() - t0
+    info = b.info()
+    _, dts, steps = b.times()
+    b.close()
+    # plain path: one handle per instance, fam_step per instance and step
+    plain_steps = 5
+    solvers = []
+    for (k, U), n in zip(insts, nx):
+        sv = fam.Solver(1, n, k=k, equation=fam.EULER, bc=fam.OUTFLOW)
+        sv.set_state(U)
+        sv.step(0.3)  # first step size + warm-up
+        solvers.append(sv)
+    for sv in solvers:
+        sv.sync()
+    t0 = time.perf_counter()
+    for _ in range(plain_steps):
+        for sv in solvers:
+            sv.step(0.3)
+    for sv in solvers:
+        sv.sync()
+    plain_s = time.perf_counter() - t0
+    for sv in solvers:
+        sv.close()
+    bv = 3.0 * cells * a.batched_steps / batched_s
+    pv = 3.0 * cells * plain_steps / plain_s
+    return {"workload": "4096 x 1D Euler, N log-uniform [64,16384], k in {3,4,5,6}, outflow, CFL 0.3, "
+                        "Riemann data (rho [0.7,1.5], |u| <= 0.3, p [0.7,2]), FP64", "instances": len(nx),
+            "cells": cells,
+            "steps": a.batched_steps, "value": bv, "unit": UNIT, "seconds": batched_s,
+            "launch": {"tile_x": info["tile_x"], "grid_blocks": info["grid"], "tiles": info["tiles"],
+                       "blocks_per_sm": bps, "kernel_launches": 1},
+            "plain_loop": {"value": pv, "unit": UNIT, "steps": plain_steps, "seconds": plain_s,
+                           "kernel_launches": 4 * len(nx) * plain_steps},
+            "speedup_vs_plain": bv / pv, "all_instances_advanced": bool(np.all(steps == a.batched_steps)),
+            "status": status,
+            "dt_spread": [float(np.min(dts)), float(np.max(dts))]}
+
+
+def adjoint_report(a, torch):
+    """Gradient of dx dy sum(rho) over a 64x64 window after 200 steps (1024^2,
+    FAM5, FP64, checkpoints every 20) against the plain forward run."""
+    from paper_2609_26194_b300 import fam, inputs
+    n, nsteps, cfl = 1024, a.adjoint_steps, 0.55
+    U0 = inputs.euler2d_fourier(n, seed=5)
+    G = np.zeros_like(U0)
+    G[0, 0, 480:544, 480:544] = 1.0 / (n * n)
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    s.set_state(U0)
+    s.run_steps(2, cfl)
+    s.sync()
+    s.set_state(U0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.run_steps(nsteps, cfl)
+    s.sync()
+    fwd_s = time.perf_counter() - t0
+    torch.cuda.reset_peak_memory_stats()
+    t0 = time.perf_counter()
+    grad = s.adjoint(U0, G, nsteps, cfl, ckpt_every=20)
+    adj_s = time.perf_counter() - t0
+    s.close()
+    state_gb = U0.nbytes / 1e9
+    return {"workload": "2D Euler FAM5 periodic 1024x1024, 200 steps, CFL 0.55, J = dx dy sum rho over "
+                        "cells [480,544)^2, checkpoints every 20", "forward_seconds": fwd_s,
+            "forward_plus_reverse_seconds": adj_s, "ratio_vs_plain_forward": adj_s / fwd_s,
+            "forward_value": 3.0 * n * n * nsteps / fwd_s, "unit": UNIT,
+            "device_memory_gb_estimate": round(state_gb * (1.05 * (nsteps // 20 + 4 * 20 + 3) + 12), 2),
+            "grad_norm_inf": float(np.max(np.abs(grad)))}
+
+
 def run_fam(a):
     import torch
     from paper_2609_26194_b300 import fam, inputs
@@ -207,12 +320,8 @@ def run_fam(a):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x: float) -> float:
+        return max_over_ranks(x, dist, "cuda")
 
     n, k, prec = a.n, a.k, a.precision
     cfl = cfl_of(a)
@@ -245,9 +354,9 @@ def run_fam(a):
     ck = clocks.stop() if clocks else None
     s.sync()
     kern_ms, prof_steps = s.profile()
-    ms = max_over_ranks(ms)
+    ms = max_ranks(ms)
     cells = n * n
-    value = world * 3.0 * cells * a.steps / (ms * 1e-3)
+    value = replica_value(world, cells, a.steps, ms)
 
     # end to end through the C ABI with host buffers: per step, H2D of the
     # state from pinned memory, one FAM step, D2H of the state
@@ -261,7 +370,7 @@ def run_fam(a):
         s.step(cfl)
         s.get_state(host_out.numpy())
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_ranks(time.perf_counter() - t0)
     state_bytes = U.nbytes
     e2e = {"value": world * 3.0 * cells * a.e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
@@ -301,6 +410,10 @@ def run_fam(a):
             "kernel_ms": {"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
                           "stage3": kern_ms[2] / max(1, prof_steps), "oe": oe_ms},
             "e2e": e2e, "gpu_launches": 4 * a.steps, "clocks": ck}
+    if rank == 0 and world == 1 and not a.no_batched:
+        line["batched"] = batched_report(a, torch)
+    if rank == 0 and world == 1 and not a.no_adjoint:
+        line["adjoint"] = adjoint_report(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb, _ = oracle_rate(a, 15.0)
         line["cpu_baseline"] = cb

@@ -72,7 +72,9 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
                       int precision, void* stream);
 
 /* Set an option (before or between steps).  Keys:
- *   "oe_type"    0 = no OE, 2 = Type II (default; Tab. sigma1d / sigma2d)
+ *   "oe_type"    0 = no OE, 1 = Type I (grid-wide mean and maximum deviation
+ *                of the cell averages), 2 = Type II (default); Tab. sigma1d /
+ *                sigma2d
  *   "gamma_k"    OE constant; <= 0 restores the paper's defaults (1D: 25 for
  *                k = 3,4 and 12.5 for k = 5,6; 2D: 25 and 15; Sec. 2.1/2.2)
  *   "oe_jump_q6" 2D k = 6 only: 1 (default) takes the OE jumps from the full
@@ -81,11 +83,22 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
  *   "smooth_dt"  1: time step with dx^(k/3) (smooth runs, Sec. 4); 0: dx
  *   "ax", "ay"   advection speeds (FAM_ADVECTION)
  *   "dt_max"     upper bound on the step size (<= 0: none)
+ *   "tile2d"     2D tile shape of the stage / OE kernels: 0 = 32 x 8 (default),
+ *                1 = 32 x 4, 2 = 16 x 8 cells (see fam_tune)
  *   "profile"    1: fam_step() brackets each of its four kernel launches with
  *                CUDA events (read with fam_profile); setting it resets the
  *                accumulated times
  * Errors: FAM_E_INVAL (unknown key or value), FAM_E_UNSUPPORTED. */
 fam_status fam_set_option(fam_t h, const char* key, double value);
+
+/* Boundary condition of one side (Remark in Sec. 2.3): side 0 = x-low,
+ * 1 = x-high, 2 = y-low, 3 = y-high; bc: 0 periodic (both sides of a
+ * direction), 1 outflow, 2 reflective wall (mirror image: the normal
+ * momentum and the moment along the normal change sign), 3 inflow (ghost
+ * averages = inflow_state[0..ncomp-1] in conservative variables, ghost
+ * moments zero).  Inflow next to a reflective wall is not built
+ * (FAM_E_UNSUPPORTED).  Errors: FAM_E_INVAL. */
+fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state);
 
 /* Copy a state in (layout above).  on_device = 0: U is host memory;
  * 1: U is device memory of the handle's device.  Resets the clock to t = 0
@@ -111,6 +124,19 @@ fam_status fam_run_steps(fam_t h, long nsteps, double cfl);
  * max_steps steps if max_steps > 0.  Synchronous.  *nsteps_out (may be NULL)
  * receives the number of steps taken by this call. */
 fam_status fam_run(fam_t h, double T, double cfl, long max_steps, long* nsteps_out);
+
+/* Enqueue nsteps steps with prescribed step sizes dts[0..nsteps-1] (host
+ * array) instead of the CFL rule -- e.g. to replay a recorded step-size
+ * sequence.  Asynchronous. */
+fam_status fam_run_fixed(fam_t h, long nsteps, const double* dts);
+
+/* Autotuner (not in the paper): times probe_steps steps of each 2D tile
+ * shape on the handle's current state (restored afterwards, clock included),
+ * keeps the fastest and appends it to cache_path (if not NULL) keyed by GPU
+ * name, equation, order, precision and grid; a cached entry is reused
+ * without timing.  *choice (may be NULL) receives the "tile2d" index.  1D
+ * handles have one shape (choice 0).  Synchronous. */
+fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path, int* choice);
 
 /* Wait for the handle's stream and report device-side status flags. */
 fam_status fam_sync(fam_t h);
@@ -143,6 +169,21 @@ const char* fam_status_string(fam_status s);
 
 /* Release all resources of h (NULL is ignored). */
 void fam_destroy(fam_t h);
+
+/* Adjoint (not in the paper; the reverse sweep of the time step).  Runs
+ * nsteps steps (eq. 12 + OE) from U0 with the CFL step sizes of Sec. 4, then
+ * returns in dJdU0 the gradient of a terminal functional J(U^T) with respect
+ * to all initial averages and moments, given dJdUT = dJ/dU^T (both in the
+ * state layout above).  The step sizes of the forward run are held fixed in
+ * the reverse sweep.  The forward states are checkpointed every ckpt_every
+ * steps and each segment is recomputed once in the reverse sweep (memory:
+ * nsteps/ckpt_every + 4*ckpt_every padded states).  Subgradients: |x| ->
+ * sign(x), a maximum -> the first maximiser (left/bottom trace, lowest
+ * component, row-major stencil order).  On return the handle's state is
+ * U^T.  Built for 2D Euler, FP64, periodic grids (FAM_E_UNSUPPORTED
+ * otherwise).  on_device as in fam_set_state.  Synchronous. */
+fam_status fam_adjoint(fam_t h, long nsteps, double cfl, int ckpt_every, const void* U0, const void* dJdUT,
+                       void* dJdU0, int on_device);
 
 /* ------------------------------------------------------------------------
  * Batched 1D problems (not in the paper: many independent instances in one

@@ -38,7 +38,8 @@ def units():
     out = [("fam_api", os.path.join(CSRC, "fam_api.cu"), []),
            ("fam_probe", os.path.join(CSRC, "fam_probe.cu"), []),
            ("fam_batch", os.path.join(CSRC, "fam_batch.cu"), []),
-           ("fam_noalloc", os.path.join(CSRC, "fam_noalloc.cu"), [])]
+           ("fam_noalloc", os.path.join(CSRC, "fam_noalloc.cu"), []),
+           ("fam_adjoint2d", os.path.join(CSRC, "fam_adjoint2d.cu"), [])]
     for d in (1, 2):
         for p in (64, 32):
             for k in (3, 4, 5, 6):
@@ -73,7 +74,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             objs.append(obj)
             if not cached:
                 logs.append((name, log))
-    if logs or not os.path.exists(LIB) or force:
+    stale = (not os.path.exists(LIB)) or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(LIB)
+    if logs or stale or force:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <string>
@@ -63,6 +64,42 @@ __global__ void fill_ghosts_kernel(T* U, const Geo geo, int np) {
   }
 }
 
+// Inflow ghosts (both layers of a side, corners included): the prescribed
+// averages, zero moments (Remark in Sec. 2.3).
+template <typename T>
+__global__ void fill_inflow_kernel(T* U, const Geo geo, int side, int nc, const double4 st) {
+  const int gx = geo.px, gy = geo.rows;
+  const double sv[4] = {st.x, st.y, st.z, st.w};
+  const long long n = (long long)gx * gy;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(q % gx), y = (int)(q / gx);
+    bool in;
+    if (side == 0) in = x < G;
+    else if (side == 1) in = x >= geo.nx + G && x < geo.nx + 2 * G;
+    else if (side == 2) in = gy > 1 && y < G;
+    else in = gy > 1 && y >= geo.ny + G && y < geo.ny + 2 * G;
+    if (!in) continue;
+    for (int c = 0; c < nc; ++c)
+      for (int m = 0; m < geo.nm; ++m) U[(long long)(c * geo.nm + m) * geo.plane + q] = m == 0 ? T(sv[c]) : T(0);
+  }
+}
+
+static fam_status fill_inflow(fam_handle* h) {
+  for (int side = 0; side < 4; ++side) {
+    if (h->geo.bc[side] != kBcInflow) continue;
+    const double* s = h->inflow[side];
+    const double4 st = make_double4(s[0], s[1], s[2], s[3]);
+    for (int b = 0; b < 3; ++b) {
+      if (h->prec == 64)
+        fill_inflow_kernel<double><<<148 * 4, 256, 0, h->stream>>>(bufp<double>(h, b), h->geo, side, h->nc, st);
+      else
+        fill_inflow_kernel<float><<<148 * 4, 256, 0, h->stream>>>(bufp<float>(h, b), h->geo, side, h->nc, st);
+      FAM_CUDA(h, cudaGetLastError());
+    }
+  }
+  return FAM_OK;
+}
+
 static fam_status fill_ghosts(fam_handle* h, int b) {
   long long n = (long long)h->geo.nx * h->geo.ny * h->np;
   int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
@@ -83,7 +120,7 @@ static fam_status encode_maps(fam_handle* h) {
     if (h->d == 2) {
       cuuint64_t dims[3] = {(cuuint64_t)h->geo.px, (cuuint64_t)h->geo.rows, (cuuint64_t)h->np};
       cuuint64_t strides[2] = {(cuuint64_t)h->geo.px * h->elem, (cuuint64_t)h->geo.plane * h->elem};
-      cuuint32_t box[3] = {TX2 + 4, TY2 + 4, (cuuint32_t)h->np};
+      cuuint32_t box[3] = {(cuuint32_t)h->ops.tx + 4, (cuuint32_t)h->ops.ty + 4, (cuuint32_t)h->np};
       cuuint32_t es[3] = {1, 1, 1};
       r = enc(&h->tm[b], dt, 3, h->buf[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -146,10 +183,34 @@ static fam_status refresh_dt(fam_handle* h, double cfl, double T, bool reset_clo
   return FAM_OK;
 }
 
+// Type-I OE: grid statistics of the averages of buffer b before the OE kernel
+static fam_status enqueue_typeI(fam_handle* h, int b) {
+  if (h->oe_type != 1) return FAM_OK;
+  const size_t off = offsetof(FamCtl, t1_maxabs_bits);
+  FAM_CUDA(h, cudaMemsetAsync(reinterpret_cast<char*>(h->ctl) + off, 0, 2 * 4 * sizeof(unsigned long long),
+                              h->stream));
+  const long long n = (long long)h->geo.nx * h->geo.ny;
+  if (h->prec == 64) {
+    typeI_partial<double, 256><<<h->t1_blocks, 256, 0, h->stream>>>(bufp<double>(h, b), h->geo, h->nc, h->nm,
+                                                                    h->t1_partial, h->ctl);
+    typeI_final<<<1, 32, 0, h->stream>>>(h->t1_partial, h->t1_blocks, h->nc, n, h->ctl);
+    typeI_dev<double, 256><<<h->t1_blocks, 256, 0, h->stream>>>(bufp<double>(h, b), h->geo, h->nc, h->nm, h->ctl);
+  } else {
+    typeI_partial<float, 256><<<h->t1_blocks, 256, 0, h->stream>>>(bufp<float>(h, b), h->geo, h->nc, h->nm,
+                                                                   h->t1_partial, h->ctl);
+    typeI_final<<<1, 32, 0, h->stream>>>(h->t1_partial, h->t1_blocks, h->nc, n, h->ctl);
+    typeI_dev<float, 256><<<h->t1_blocks, 256, 0, h->stream>>>(bufp<float>(h, b), h->geo, h->nc, h->nm, h->ctl);
+  }
+  FAM_CUDA(h, cudaGetLastError());
+  return FAM_OK;
+}
+
 static fam_status enqueue_step(fam_handle* h) {
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
+  fam_status s = enqueue_typeI(h, 1);
+  if (s) return s;
   FAM_CUDA(h, h->ops.oe(h, 1, 0, -1.0));
   return FAM_OK;
 }
@@ -177,10 +238,33 @@ static fam_status enqueue_step_profiled(fam_handle* h) {
   FAM_CUDA(h, cudaEventRecord(e[2], h->stream));
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   FAM_CUDA(h, cudaEventRecord(e[3], h->stream));
+  fam_status s = enqueue_typeI(h, 1);
+  if (s) return s;
   FAM_CUDA(h, h->ops.oe(h, 1, 0, -1.0));
   FAM_CUDA(h, cudaEventRecord(e[4], h->stream));
   return FAM_OK;
 }
+
+// One step with a prescribed step size (adjoint recomputation).  If store is
+// not null, the stage inputs U^n, U^(1), U^(2) and the pre-OE state U^(3)
+// are copied into store[0..3] (padded buffers).
+fam_status fam_internal_step_fixed_dt(fam_handle* h, double dt, void* const* store) {
+  const size_t sb = h->buf_elems * h->elem;
+  FAM_CUDA(h, cudaMemcpyAsync(&h->ctl->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (store) FAM_CUDA(h, cudaMemcpyAsync(store[0], h->buf[0], sb, cudaMemcpyDeviceToDevice, h->stream));
+  FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
+  if (store) FAM_CUDA(h, cudaMemcpyAsync(store[1], h->buf[1], sb, cudaMemcpyDeviceToDevice, h->stream));
+  FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
+  if (store) FAM_CUDA(h, cudaMemcpyAsync(store[2], h->buf[2], sb, cudaMemcpyDeviceToDevice, h->stream));
+  FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
+  if (store) FAM_CUDA(h, cudaMemcpyAsync(store[3], h->buf[1], sb, cudaMemcpyDeviceToDevice, h->stream));
+  fam_status st = enqueue_typeI(h, 1);
+  if (st) return st;
+  FAM_CUDA(h, h->ops.oe(h, 1, 0, -1.0));
+  return FAM_OK;
+}
+
+fam_status refresh_dt_public(fam_handle* h, double cfl) { return refresh_dt(h, cfl, 0.0, false); }
 
 static fam_status ensure_dt(fam_handle* h, double cfl, double T) {
   if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
@@ -218,6 +302,7 @@ void fam_destroy(fam_t h) {
   for (int b = 0; b < 3; ++b)
     if (h->buf[b]) cudaFree(h->buf[b]);
   if (h->ctl) cudaFree(h->ctl);
+  if (h->t1_partial) cudaFree(h->t1_partial);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -255,6 +340,9 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
   g.rows = grid->d == 2 ? g.ny + 2 * G : 1;
   g.plane = (long long)g.px * g.rows;
   g.bcx = g.bcy = bc;
+  for (int q = 0; q < 4; ++q) g.bc[q] = bc;
+  g.nm = h->nm;
+  g.euler = equation == FAM_EULER;
   g.dx = (grid->x1 - grid->x0) / grid->nx;
   g.dy = grid->d == 2 ? (grid->y1 - grid->y0) / grid->ny : 1.0;
   g.idx = 1.0 / g.dx;
@@ -295,6 +383,11 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
     fam_destroy(h);
     return FAM_E_NOMEM;
   }
+  h->t1_blocks = (int)std::max<long long>(1, std::min<long long>(((long long)g.nx * g.ny + 255) / 256, 148LL * 4));
+  if (cudaMalloc(&h->t1_partial, sizeof(double) * 4 * h->t1_blocks) != cudaSuccess) {
+    fam_destroy(h);
+    return FAM_E_NOMEM;
+  }
   cudaMemsetAsync(h->ctl, 0, sizeof(FamCtl), h->stream);
   if (encode_maps(h) != FAM_OK) {
     fam_destroy(h);
@@ -308,13 +401,108 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
   return FAM_OK;
 }
 
+// Bind the 2D kernels of tile shape kTile2D[t] and re-encode the TMA boxes.
+static fam_status select_tile(fam_handle* h, int t) {
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->tile2d = t;
+  if (!pick(h)) return fail(h, FAM_E_UNSUPPORTED, "no kernels for this configuration");
+  FAM_CUDA(h, h->ops.prepare());
+  fam_status s = encode_maps(h);
+  if (s) return s;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  return FAM_OK;
+}
+
+fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path, int* choice) {
+  if (!h) return FAM_E_INVAL;
+  if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
+  if (h->d != 2) {
+    if (choice) *choice = 0;
+    return FAM_OK;  // 1D kernels have a single tile shape
+  }
+  if (probe_steps < 1) probe_steps = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  char key[512];
+  std::snprintf(key, sizeof(key), "%s|2d|eq%d|k%d|p%d|%dx%d", prop.name, h->eq, h->k, h->prec, h->geo.nx, h->geo.ny);
+  if (cache_path && cache_path[0]) {
+    FILE* f = std::fopen(cache_path, "r");
+    if (f) {
+      char line[600];
+      while (std::fgets(line, sizeof(line), f)) {
+        char* tab = std::strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        if (std::strcmp(line, key) == 0) {
+          const int t = std::atoi(tab + 1);
+          std::fclose(f);
+          if (t < 0 || t > 2) break;
+          if (choice) *choice = t;
+          return select_tile(h, t);
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  const size_t sb = h->buf_elems * h->elem;
+  void* save = nullptr;
+  FAM_CUDA(h, cudaMalloc(&save, sb));
+  FAM_CUDA(h, cudaMemcpyAsync(save, h->buf[0], sb, cudaMemcpyDeviceToDevice, h->stream));
+  FamCtl ctl_save;
+  fam_status s = ctl_read(h, &ctl_save);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = h->tile2d;
+  float best_ms = 1e30f;
+  for (int t = 0; t < 3 && s == FAM_OK; ++t) {
+    if (select_tile(h, t) != FAM_OK) continue;
+    cudaMemcpyAsync(h->buf[0], save, sb, cudaMemcpyDeviceToDevice, h->stream);
+    if (refresh_dt(h, cfl, 0.0, true) != FAM_OK) continue;
+    enqueue_step(h);  // warm-up
+    cudaMemcpyAsync(h->buf[0], save, sb, cudaMemcpyDeviceToDevice, h->stream);
+    if (refresh_dt(h, cfl, 0.0, true) != FAM_OK) continue;
+    cudaEventRecord(e0, h->stream);
+    for (int q = 0; q < probe_steps; ++q) enqueue_step(h);
+    cudaEventRecord(e1, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  fam_status s2 = select_tile(h, best);
+  cudaMemcpyAsync(h->buf[0], save, sb, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->ctl, &ctl_save, sizeof(FamCtl), cudaMemcpyHostToDevice, h->stream);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(save);
+  h->dt_valid = false;
+  if (s) return s;
+  if (s2) return s2;
+  if (cache_path && cache_path[0]) {
+    FILE* f = std::fopen(cache_path, "a");
+    if (f) {
+      std::fprintf(f, "%s\t%d\n", key, best);
+      std::fclose(f);
+    }
+  }
+  if (choice) *choice = best;
+  return FAM_OK;
+}
+
 fam_status fam_set_option(fam_t h, const char* key, double v) {
   if (!h || !key) return FAM_E_INVAL;
   std::string k(key);
   if (k == "oe_type") {
-    if (v == 0.0 || v == 2.0) h->oe_type = (int)v;
-    else if (v == 1.0) return fail(h, FAM_E_UNSUPPORTED, "Type-I OE is not built in the CUDA path");
-    else return fail(h, FAM_E_INVAL, "oe_type must be 0 or 2");
+    if (v == 0.0 || v == 1.0 || v == 2.0) h->oe_type = (int)v;
+    else return fail(h, FAM_E_INVAL, "oe_type must be 0, 1 or 2");
   } else if (k == "gamma_k") {
     h->gamma_k = v;
   } else if (k == "oe_jump_q6") {
@@ -327,6 +515,10 @@ fam_status fam_set_option(fam_t h, const char* key, double v) {
     h->ay = v;
   } else if (k == "dt_max") {
     h->dt_max = v;
+  } else if (k == "tile2d") {
+    if (h->d != 2) return fail(h, FAM_E_INVAL, "tile2d applies to 2D grids");
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, FAM_E_INVAL, "tile2d must be 0, 1 or 2");
+    return select_tile(h, (int)v);
   } else if (k == "profile") {
     h->profile = v != 0.0;
     h->ev_used = 0;
@@ -370,6 +562,38 @@ static fam_status copy_out(fam_handle* h, void* U, int on_device, int b) {
     FAM_CUDA(h, cudaMemcpy2DAsync(dst + p * dst_plane, row, s0, (size_t)g.px * h->elem, row, g.ny, kind, h->stream));
   }
   if (!on_device) FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state) {
+  if (!h || side < 0 || side > 3 || bc < kBcPeriodic || bc > kBcInflow) return FAM_E_INVAL;
+  if (side >= 2 && h->d == 1) return fail(h, FAM_E_INVAL, "1D grids have only the x sides");
+  if (bc == kBcInflow && !inflow_state) return fail(h, FAM_E_INVAL, "inflow needs a state");
+  int nb[4] = {h->geo.bc[0], h->geo.bc[1], h->geo.bc[2], h->geo.bc[3]};
+  nb[side] = bc;
+  for (int dir = 0; dir < h->d; ++dir)
+    if ((nb[2 * dir] == kBcPeriodic) != (nb[2 * dir + 1] == kBcPeriodic))
+      return fail(h, FAM_E_INVAL, "periodic conditions come in pairs; set the opposite side too");
+  if (h->d == 2)
+    for (int dir = 0; dir < 2; ++dir)
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (nb[2 * dir + s2] == kBcInflow && (nb[2 * (1 - dir)] == kBcReflective || nb[2 * (1 - dir) + 1] == kBcReflective))
+          return fail(h, FAM_E_UNSUPPORTED, "inflow next to a reflective wall is not built");
+  for (int q = 0; q < 4; ++q) h->geo.bc[q] = nb[q];
+  h->geo.bcx = nb[0];
+  h->geo.bcy = nb[2];
+  if (bc == kBcInflow)
+    for (int c = 0; c < h->nc; ++c) h->inflow[side][c] = inflow_state[c];
+  fam_status s = fill_inflow(h);
+  if (s) return s;
+  if (h->have_state) {
+    s = fill_ghosts(h, 0);
+    if (s) return s;
+  }
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->dt_valid = false;
   return FAM_OK;
 }
 
@@ -422,6 +646,18 @@ fam_status fam_run_steps(fam_t h, long nsteps, double cfl) {
     it = h->graphs.emplace(nsteps, exec).first;
   }
   FAM_CUDA(h, cudaGraphLaunch(it->second, h->stream));
+  return FAM_OK;
+}
+
+fam_status fam_run_fixed(fam_t h, long nsteps, const double* dts) {
+  if (!h || (nsteps > 0 && !dts)) return FAM_E_INVAL;
+  if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
+  for (long q = 0; q < nsteps; ++q) {
+    if (!(dts[q] > 0.0)) return fail(h, FAM_E_INVAL, "step sizes must be positive");
+    fam_status s = fam_internal_step_fixed_dt(h, dts[q], nullptr);
+    if (s) return s;
+  }
+  h->dt_valid = false;  // the next CFL step recomputes its size from the state
   return FAM_OK;
 }
 
@@ -502,6 +738,8 @@ fam_status fam_oe(fam_t h, double dt, const void* U, void* Uout, int on_device) 
   if (!h) return FAM_E_INVAL;
   if (!(dt >= 0.0)) return fail(h, FAM_E_INVAL, "dt must be >= 0");
   fam_status s = copy_in(h, U, on_device, 1);
+  if (s) return s;
+  s = enqueue_typeI(h, 1);
   if (s) return s;
   FAM_CUDA(h, h->ops.oe(h, 1, 2, dt));
   s = copy_out(h, Uout, on_device, 2);

@@ -104,6 +104,9 @@ __device__ __forceinline__ Geo geo_of(const BatchInst& I, int bc) {
   g.rows = 1;
   g.plane = I.px;
   g.bcx = g.bcy = bc;
+  for (int q = 0; q < 4; ++q) g.bc[q] = bc;
+  g.nm = 2;
+  g.euler = 1;
   g.dx = I.dx;
   g.dy = 1.0;
   g.idx = I.idx;
@@ -216,6 +219,9 @@ __global__ void fill_ghosts_batch(T* U, const BatchInst* inst, int ninst, int np
     const BatchInst I = inst[i];
     Geo geo;
     geo.nx = I.nx; geo.ny = 1; geo.px = I.px; geo.rows = 1; geo.plane = I.px; geo.bcx = geo.bcy = bc;
+    for (int q = 0; q < 4; ++q) geo.bc[q] = bc;
+    geo.nm = 2;
+    geo.euler = 1;
     geo.dx = I.dx; geo.dy = 1.0; geo.idx = I.idx; geo.idy = 1.0;
     for (int q = threadIdx.x; q < np * I.nx; q += blockDim.x) {
       const int p = q / I.nx, c = q % I.nx;

@@ -39,6 +39,11 @@ struct FamCtl {
   unsigned int status;
   int final_step;         // current dt was clamped to reach T
   int dim;                // 1 or 2
+  // Type-I OE (Tab. sigma1d / sigma2d): per component, the bit patterns of
+  // max |u_p| and of D_Omega = max |u_p - mean| over the grid, and the mean
+  unsigned long long t1_maxabs_bits[4];
+  unsigned long long t1_dev_bits[4];
+  double t1_mean[4];
 };
 
 // Padded structure-of-arrays layout.  Plane p = c * nmom + m; within a
@@ -50,10 +55,26 @@ struct Geo {
   int px;            // row pitch in elements (>= nx + 2G, multiple of 4)
   int rows;          // ny + 2G in 2D, 1 in 1D
   long long plane;   // elements per plane = px * rows
-  int bcx, bcy;      // 0 periodic, 1 outflow
+  int bcx, bcy;      // boundary condition on every side of a direction (0 periodic, 1 outflow)
   double dx, dy;
   double idx, idy;   // 1/dx, 1/dy
+  // per-side conditions (x-lo, x-hi, y-lo, y-hi): 0 periodic, 1 outflow,
+  // 2 reflective wall, 3 inflow (ghosts hold a fixed state, written once)
+  int bc[4];
+  int nm;            // moments per component (planes p = c * nm + m)
+  int euler;         // component 1 + dir is the normal momentum of a wall
 };
+
+enum { kBcPeriodic = 0, kBcOutflow = 1, kBcReflective = 2, kBcInflow = 3 };
+
+// Sign of plane (c, m) in the mirror image across a wall normal to dir: the
+// normal momentum and the moment along the normal flip (both: no flip).
+__host__ __device__ inline int reflect_sign(const Geo& g, int plane, int dir) {
+  const int c = plane / g.nm, m = plane % g.nm;
+  const bool normal_mom = g.euler && c == 1 + dir;
+  const bool normal_moment = m == 1 + dir;
+  return normal_mom != normal_moment ? -1 : 1;
+}
 
 __host__ __device__ inline long long cell_index(const Geo& g, int plane, int j, int i) {
   return (long long)plane * g.plane + (long long)((g.rows > 1 ? j + G : 0)) * g.px + (i + G);

@@ -27,11 +27,16 @@ bool FAM_PICK_NAME(fam_handle* h) {
     case FAM_EULER: h->ops = ops_of<Impl1D<Real, K, Euler1D<Real>>>(); return true;
   }
 #else
-  switch (h->eq) {
-    case FAM_ADVECTION: h->ops = ops_of<Impl2D<Real, K, Advection2D<Real>>>(); return true;
-    case FAM_BURGERS: h->ops = ops_of<Impl2D<Real, K, Burgers2D<Real>>>(); return true;
-    case FAM_EULER: h->ops = ops_of<Impl2D<Real, K, Euler2D<Real>>>(); return true;
+#define FAM_PICK2D(TXv, TYv)                                                                           \
+  switch (h->eq) {                                                                                      \
+    case FAM_ADVECTION: h->ops = ops_of2d<Impl2D<Real, K, Advection2D<Real>, TXv, TYv>>(); return true; \
+    case FAM_BURGERS: h->ops = ops_of2d<Impl2D<Real, K, Burgers2D<Real>, TXv, TYv>>(); return true;     \
+    case FAM_EULER: h->ops = ops_of2d<Impl2D<Real, K, Euler2D<Real>, TXv, TYv>>(); return true;         \
   }
+  if (h->tile2d == 1) { FAM_PICK2D(32, 4) }
+  else if (h->tile2d == 2) { FAM_PICK2D(16, 8) }
+  else { FAM_PICK2D(32, 8) }
+#undef FAM_PICK2D
 #endif
   return false;
 }

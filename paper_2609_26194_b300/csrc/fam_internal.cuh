@@ -17,13 +17,17 @@
 using namespace fam;
 
 // tile shapes
-constexpr int TX2 = 32, TY2 = 8;   // 2D: 256 threads, one cell each
+// 2D tile shapes (one thread per cell), chosen by option "tile2d" or fam_tune:
+//   0: 32 x 8 (256 threads, 1 block/SM), 1: 32 x 4 (128 threads, 2 blocks/SM),
+//   2: 16 x 8 (128 threads, 2 blocks/SM)
+constexpr int kTile2D[3][2] = {{32, 8}, {32, 4}, {16, 8}};
 constexpr int TX1 = 128;           // 1D: 128 cells per block
 
 // ---------------------------------------------------------------------------
 // per-configuration launchers
 // ---------------------------------------------------------------------------
 struct Ops {
+  int tx = 0, ty = 0;  // tile of the 2D kernels (box of the TMA descriptors)
   cudaError_t (*stage)(struct fam_handle*, int in, int u0, int out, int stage);
   cudaError_t (*oe)(struct fam_handle*, int in, int out, double dt_override);
   cudaError_t (*alpha)(struct fam_handle*, int buf);
@@ -45,6 +49,9 @@ struct fam_handle {
   size_t buf_elems = 0;
   void* buf[3] = {nullptr, nullptr, nullptr};
   FamCtl* ctl = nullptr;
+  double inflow[4][4] = {{0}};   // inflow states per side (conservative averages)
+  double* t1_partial = nullptr;  // Type-I OE block partial sums
+  int t1_blocks = 0;
   CUtensorMap tm[3];
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -55,6 +62,7 @@ struct fam_handle {
   std::map<long, cudaGraphExec_t> graphs;
   Ops ops{};
   std::string err;
+  int tile2d = 0;  // index into kTile2D
   // opt-in per-kernel timing (option "profile"): 5 events per step bracket
   // the three stage launches and the OE launch of fam_step()
   bool profile = false;
@@ -111,8 +119,9 @@ inline double default_gamma_k(const fam_handle* h) {
   return h->d == 1 ? 12.5 : 15.0;
 }
 
-template <typename T, int K, class PH>
+template <typename T, int K, class PH, int TX2, int TY2>
 struct Impl2D {
+  static constexpr int kTX = TX2, kTY = TY2;
   using S = Smem2D<T, PH::NC, TX2, TY2>;
   static cudaError_t prepare() {
     cudaError_t e = cudaFuncSetAttribute(stage2d<T, K, PH, TX2, TY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -171,7 +180,8 @@ struct Impl1D {
   }
 };
 
-template <class I> Ops ops_of() { return Ops{&I::stage, &I::oe, &I::alpha, &I::prepare}; }
+template <class I> Ops ops_of() { return Ops{0, 0, &I::stage, &I::oe, &I::alpha, &I::prepare}; }
+template <class I> Ops ops_of2d() { return Ops{I::kTX, I::kTY, &I::stage, &I::oe, &I::alpha, &I::prepare}; }
 
 // per-configuration selectors, one per instantiation unit (fam_inst.cu)
 #define FAM_DECL_PICK(D, P, K) bool fam_pick_d##D##_p##P##_k##K(fam_handle* h);
@@ -182,3 +192,7 @@ FAM_DECL_PICK_K(2, 64)
 FAM_DECL_PICK_K(2, 32)
 #undef FAM_DECL_PICK_K
 #undef FAM_DECL_PICK
+
+// shared host helpers (fam_api.cu)
+fam_status refresh_dt_public(fam_handle* h, double cfl);
+fam_status fam_internal_step_fixed_dt(fam_handle* h, double dt, void* const* store);

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(TX)
 template <typename T, int K, class PH, int TX>
 __device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __restrict__ Uout, const Geo& geo,
                                             const PH& ph, const T dt, const int oe_type, const T gamma_k,
-                                            const int x0, unsigned int* status) {
+                                            const int x0, unsigned int* status, const FamCtl* ctl = nullptr) {
   constexpr int NC = PH::NC;
   constexpr int HX = TX + 4;
   constexpr int D = K - 1;
@@ -201,9 +201,15 @@ __device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __re
       const T jr = tr[((q + 1) * 2 + 0) * NC + c] - tr[(q * 2 + 1) * NC + c];
       const T* pa = tile + (size_t)(c * 2) * HX;
       const T vm = pa[hx - 1], v0 = pa[hx], vp = pa[hx + 1];
-      const T S = vm + v0 + vp;
-      const T Dn = fmax(fmax(fabs(vm - S), fabs(v0 - S)), fabs(vp - S));
-      const T eps = T(1e-14) * fmax(fmax(fmax(fabs(vm), fabs(v0)), fabs(vp)), T(1));
+      T Dn, eps;
+      if (oe_type == 1) {
+        Dn = T(__longlong_as_double((long long)ctl->t1_dev_bits[c]));
+        eps = T(1e-14) * fmax(T(__longlong_as_double((long long)ctl->t1_maxabs_bits[c])), T(1));
+      } else {
+        const T S = vm + v0 + vp;
+        Dn = fmax(fmax(fabs(vm - S), fabs(v0 - S)), fabs(vp - S));
+        eps = T(1e-14) * fmax(fmax(fmax(fabs(vm), fabs(v0)), fabs(vp)), T(1));
+      }
       if (oe_type != 0 && !(Dn < eps)) sig = fmax(sig, gamma_k * (fabs(jl) + fabs(jr)) * Fast<T>::rcp(Dn));
     }
     const T beta = fmax(fmax(sp[q - 1], sp[q]), sp[q + 1]);
@@ -247,12 +253,72 @@ __global__ void __launch_bounds__(TX)
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;
   const double my_speed =
-      oe1d_tile<T, K, PH, TX>(tile, tr, sp, Uout, geo, ph, T(dtd), oe_type, gamma_k, x0, &ctl->status);
+      oe1d_tile<T, K, PH, TX>(tile, tr, sp, Uout, geo, ph, T(dtd), oe_type, gamma_k, x0, &ctl->status, ctl);
   if (!reduce) return;
   const double mx = block_max<TX>(my_speed, red);
   if (threadIdx.x == 0) {
     atomic_max_nonneg(&ctl->alpha_bits[0], mx);
     step_epilogue(ctl, gridDim.x, true);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Type-I OE denominators (Tab. sigma1d / sigma2d): grid mean, max |u| and
+// D_Omega = max |u - mean| of the cell averages per component.  The sum is
+// deterministic: fixed-order block partials, summed in order by one block.
+// ---------------------------------------------------------------------------
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) typeI_partial(const T* __restrict__ U, const Geo geo, int nc, int nm,
+                                                    double* __restrict__ partial, FamCtl* __restrict__ ctl) {
+  __shared__ double sh[NT];
+  const long long n = (long long)geo.nx * geo.ny;
+  for (int c = 0; c < nc; ++c) {
+    double s = 0.0, mabs = 0.0;
+    for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < n; q += (long long)gridDim.x * NT) {
+      const int i = (int)(q % geo.nx), j = (int)(q / geo.nx);
+      const double v = (double)U[cell_index(geo, c * nm, j, i)];
+      s += v;
+      mabs = fmax(mabs, fabs(v));
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(long long)c * gridDim.x + blockIdx.x] = sh[0];
+    __syncthreads();
+    const double m = block_max<NT>(mabs, sh);
+    if (threadIdx.x == 0) atomic_max_nonneg(&ctl->t1_maxabs_bits[c], m);
+    __syncthreads();
+  }
+}
+
+template <int UNUSED = 0>
+__global__ void typeI_final(const double* __restrict__ partial, int nblocks, int nc, long long ncells,
+                            FamCtl* __restrict__ ctl) {
+  if (threadIdx.x < nc) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(long long)threadIdx.x * nblocks + b];
+    ctl->t1_mean[threadIdx.x] = s / (double)ncells;
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) typeI_dev(const T* __restrict__ U, const Geo geo, int nc, int nm,
+                                                FamCtl* __restrict__ ctl) {
+  __shared__ double red[64];
+  const long long n = (long long)geo.nx * geo.ny;
+  for (int c = 0; c < nc; ++c) {
+    const double mean = ctl->t1_mean[c];
+    double d = 0.0;
+    for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < n; q += (long long)gridDim.x * NT) {
+      const int i = (int)(q % geo.nx), j = (int)(q / geo.nx);
+      d = fmax(d, fabs((double)U[cell_index(geo, c * nm, j, i)] - mean));
+    }
+    d = block_max<NT>(d, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&ctl->t1_dev_bits[c], d);
+    __syncthreads();
   }
 }
 

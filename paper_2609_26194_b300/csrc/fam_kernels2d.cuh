@@ -31,34 +31,38 @@ __device__ __forceinline__ void stage_weights(int stage, double& w0, double& w1)
   else { w0 = 1.0 / 3.0; w1 = 2.0 / 3.0; }
 }
 
+// Padded positions (and signs) at which interior index i of one direction
+// appears: itself and its ghost images for the two sides' conditions
+// (Remark in Sec. 2.3: periodic wrap; outflow copies the boundary cell into
+// both layers; a reflective wall mirrors the first G cells; inflow ghosts are
+// fixed and get no image).
+__device__ __forceinline__ int ghost_images(int i, int n, int lo, int hi, int sgn_refl, int* pos, int* sgn) {
+  int q = 0;
+  pos[q] = i + G; sgn[q++] = 1;
+  if (lo == kBcPeriodic) {
+    if (i < G) { pos[q] = i + G + n; sgn[q++] = 1; }
+    if (i >= n - G) { pos[q] = i + G - n; sgn[q++] = 1; }
+    return q;
+  }
+  if (lo == kBcOutflow && i == 0) { pos[q] = 0; sgn[q++] = 1; pos[q] = 1; sgn[q++] = 1; }
+  if (lo == kBcReflective && i < G) { pos[q] = G - 1 - i; sgn[q++] = sgn_refl; }
+  if (hi == kBcOutflow && i == n - 1) { pos[q] = n + G; sgn[q++] = 1; pos[q] = n + G + 1; sgn[q++] = 1; }
+  if (hi == kBcReflective && i >= n - G) { pos[q] = n + G + (n - 1 - i); sgn[q++] = sgn_refl; }
+  return q;
+}
+
 // Write v to cell (i, j) of plane p and to every ghost image of that cell.
 template <typename T>
 __device__ __forceinline__ void store_with_ghosts(T* __restrict__ out, const Geo& g, int p, int j, int i, T v) {
-  int xs[3], ys[3];
-  int nxs = 0, nys = 0;
-  xs[nxs++] = i + G;
-  if (g.bcx == 0) {
-    if (i < G) xs[nxs++] = i + G + g.nx;
-    if (i >= g.nx - G) xs[nxs++] = i + G - g.nx;
-  } else {
-    if (i == 0) { xs[nxs++] = 0; xs[nxs++] = 1; }
-    if (i == g.nx - 1) { xs[nxs++] = g.nx + G; xs[nxs++] = g.nx + G + 1; }
-  }
-  if (g.rows > 1) {
-    ys[nys++] = j + G;
-    if (g.bcy == 0) {
-      if (j < G) ys[nys++] = j + G + g.ny;
-      if (j >= g.ny - G) ys[nys++] = j + G - g.ny;
-    } else {
-      if (j == 0) { ys[nys++] = 0; ys[nys++] = 1; }
-      if (j == g.ny - 1) { ys[nys++] = g.ny + G; ys[nys++] = g.ny + G + 1; }
-    }
-  } else {
-    ys[nys++] = 0;
-  }
+  int xs[4], xsg[4], ys[4], ysg[4];
+  const int nxs = ghost_images(i, g.nx, g.bc[0], g.bc[1], reflect_sign(g, p, 0), xs, xsg);
+  int nys = 1;
+  ys[0] = 0;
+  ysg[0] = 1;
+  if (g.rows > 1) nys = ghost_images(j, g.ny, g.bc[2], g.bc[3], reflect_sign(g, p, 1), ys, ysg);
   T* base = out + (long long)p * g.plane;
   for (int b = 0; b < nys; ++b)
-    for (int a = 0; a < nxs; ++a) base[(long long)ys[b] * g.px + xs[a]] = v;
+    for (int a = 0; a < nxs; ++a) base[(long long)ys[b] * g.px + xs[a]] = (xsg[a] * ysg[b] < 0) ? -v : v;
 }
 
 // Shared-memory layout of the 2D kernels (in elements of T).
@@ -400,10 +404,15 @@ __global__ void __launch_bounds__(TX * TY, 1)
         S += v[s];
         mabs = fmax(mabs, fabs(v[s]));
       }
-      T Dn = T(0);
+      T Dn = T(0), eps;
+      if (oe_type == 1) {
+        Dn = T(__longlong_as_double((long long)ctl->t1_dev_bits[c]));
+        eps = T(1e-14) * fmax(T(__longlong_as_double((long long)ctl->t1_maxabs_bits[c])), T(1));
+      } else {
 #pragma unroll
-      for (int s = 0; s < 9; ++s) Dn = fmax(Dn, fabs(v[s] - S));
-      const T eps = T(1e-14) * fmax(mabs, T(1));
+        for (int s = 0; s < 9; ++s) Dn = fmax(Dn, fabs(v[s] - S));
+        eps = T(1e-14) * fmax(mabs, T(1));
+      }
       if (oe_type != 0 && !(Dn < eps)) {
         const T g = gamma_k * Fast<T>::rcp(Dn);
         sig_x = fmax(sig_x, g * (fabs(jxl) + fabs(jxr)));

@@ -99,6 +99,9 @@ extern "C" fam_status fam_step1d_noalloc(const void* U_in, void* U_out, int nx, 
   g.rows = 1;
   g.plane = g.px;
   g.bcx = g.bcy = bc;
+  for (int q = 0; q < 4; ++q) g.bc[q] = bc;
+  g.nm = 2;
+  g.euler = equation == FAM_EULER;
   g.dx = (x1 - x0) / nx;
   g.dy = 1.0;
   g.idx = 1.0 / g.dx;

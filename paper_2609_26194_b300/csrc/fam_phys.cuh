@@ -168,6 +168,44 @@ template <typename T> struct Euler2D {
   __device__ __forceinline__ bool admissible(const T* u) const {
     return u[0] > T(0) && u[0] * u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) > T(0);
   }
+
+  // ---- derivatives for the adjoint ------------------------------------------
+  // ub += (d f_dir / d u)^T w  (flux Jacobian-transpose product)
+  __device__ __forceinline__ void flux_vjp(int dir, const T* u, const T* w, T* ub) const {
+    const T r = T(1) / u[0];
+    const T vx = u[1] * r, vy = u[2] * r;
+    const T q2 = vx * vx + vy * vy;
+    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
+    const T H = (u[3] + p) * r;
+    if (dir == 0) {
+      ub[0] += w[1] * (hgm1 * q2 - vx * vx) - w[2] * vx * vy + w[3] * vx * (hgm1 * q2 - H);
+      ub[1] += w[0] + w[1] * (T(2) - gm1) * vx + w[2] * vy + w[3] * (H - gm1 * vx * vx);
+      ub[2] += -w[1] * gm1 * vy + w[2] * vx - w[3] * gm1 * vx * vy;
+      ub[3] += w[1] * gm1 + w[3] * g * vx;
+    } else {
+      ub[0] += -w[1] * vx * vy + w[2] * (hgm1 * q2 - vy * vy) + w[3] * vy * (hgm1 * q2 - H);
+      ub[1] += w[1] * vy - w[2] * gm1 * vx - w[3] * gm1 * vx * vy;
+      ub[2] += w[0] + w[1] * vx + w[2] * (T(2) - gm1) * vy + w[3] * (H - gm1 * vy * vy);
+      ub[3] += w[2] * gm1 + w[3] * g * vy;
+    }
+  }
+  // spectral radius |v_dir| + c and its gradient with respect to u
+  __device__ __forceinline__ T speed_grad(int dir, const T* u, T* gr) const {
+    const T r = T(1) / u[0];
+    const T vx = u[1] * r, vy = u[2] * r;
+    const T q2 = vx * vx + vy * vy;
+    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
+    const T c = sqrt(g * p * r);
+    const T vn = dir == 0 ? vx : vy;
+    const T sg = vn > T(0) ? T(1) : (vn < T(0) ? T(-1) : T(0));
+    const T kc = g / (T(2) * c * u[0]);   // dc = kc (dp - (p/rho) drho)
+    // dp/du = gm1 (q2/2, -vx, -vy, 1); dvn/du = (-vn/rho, [dir==0]/rho, [dir==1]/rho, 0)
+    gr[0] = -sg * vn * r + kc * (hgm1 * q2 - p * r);
+    gr[1] = (dir == 0 ? sg * r : T(0)) - kc * gm1 * vx;
+    gr[2] = (dir == 1 ? sg * r : T(0)) - kc * gm1 * vy;
+    gr[3] = kc * gm1;
+    return fabs(vn) + c;
+  }
 };
 
 }  // namespace fam

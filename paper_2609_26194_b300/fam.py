@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfam.so")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, REFLECTIVE, INFLOW = 0, 1, 2, 3
 STATUS = {0: "FAM_OK", 1: "FAM_E_INVAL", 2: "FAM_E_NOMEM", 3: "FAM_E_CUDA", 4: "FAM_E_NONPHYSICAL",
           5: "FAM_E_TIMEOUT", 6: "FAM_E_STATE", 7: "FAM_E_UNSUPPORTED"}
 
@@ -28,7 +28,8 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_status_string", "fam_destroy", "fam_alu_peak", "fam_selftest_math",
            "fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
            "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
-           "fam_batch_last_error", "fam_batch_destroy", "fam_step1d_noalloc")
+           "fam_batch_last_error", "fam_batch_destroy", "fam_step1d_noalloc", "fam_adjoint",
+           "fam_run_fixed", "fam_set_bc", "fam_tune")
 
 
 class FamError(RuntimeError):
@@ -66,6 +67,10 @@ def lib() -> ctypes.CDLL:
         L.fam_profile.argtypes = [vp, dp, ctypes.POINTER(l)]
         L.fam_residual.argtypes = [vp, vp, vp, i]
         L.fam_oe.argtypes = [vp, d, vp, vp, i]
+        L.fam_adjoint.argtypes = [vp, l, d, i, vp, vp, vp, i]
+        L.fam_run_fixed.argtypes = [vp, l, dp]
+        L.fam_set_bc.argtypes = [vp, i, i, dp]
+        L.fam_tune.argtypes = [vp, d, i, ctypes.c_char_p, ctypes.POINTER(i)]
         L.fam_last_error.argtypes = [vp]
         L.fam_last_error.restype = ctypes.c_char_p
         L.fam_status_string.argtypes = [i]
@@ -136,6 +141,14 @@ class Solver:
     def set_option(self, key: str, value: float):
         self._check(lib().fam_set_option(self._h, key.encode(), float(value)))
 
+    def set_bc(self, side: int, bc: int, inflow=None):
+        """Per-side condition: side 0 x-low, 1 x-high, 2 y-low, 3 y-high."""
+        st = None
+        if inflow is not None:
+            arr = (ctypes.c_double * 4)(*([float(v) for v in inflow] + [0.0] * (4 - len(inflow))))
+            st = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        self._check(lib().fam_set_bc(self._h, int(side), int(bc), st))
+
     def _buf(self, U):
         if _is_torch(U):
             if tuple(U.shape) != self.shape or not U.is_contiguous():
@@ -174,6 +187,26 @@ class Solver:
     def sync(self):
         self._check(lib().fam_sync(self._h))
 
+    def tune(self, cfl: float, probe_steps: int = 2, cache_path: str | None = None) -> int:
+        """Pick the fastest 2D tile shape on the current state (returns the index)."""
+        c = ctypes.c_int()
+        self._check(lib().fam_tune(self._h, float(cfl), int(probe_steps),
+                                   cache_path.encode() if cache_path else None, ctypes.byref(c)))
+        return c.value
+
+    def run_fixed(self, dts):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(lib().fam_run_fixed(self._h, d.size, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def record_steps(self, nsteps: int, cfl: float) -> np.ndarray:
+        """Take nsteps CFL steps one by one and return the step sizes used."""
+        out = np.empty(nsteps)
+        self.run_steps(0, cfl)  # make the device step size current without stepping
+        for q in range(nsteps):
+            out[q] = self.time()[1]
+            self.step(cfl)
+        return out
+
     def time(self) -> tuple[float, float, int]:
         t, dt, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_long()
         self._check(lib().fam_time(self._h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(s)))
@@ -191,6 +224,17 @@ class Solver:
         out = np.empty(self.shape, dtype=self.dtype) if not dev else keep.new_empty(self.shape)
         q, dev2, keep2 = self._buf(out)
         self._check(lib().fam_residual(self._h, p, q, dev))
+        return out
+
+    def adjoint(self, U0, dJdUT, nsteps: int, cfl: float, ckpt_every: int = 20):
+        """dJ/dU0 of a terminal functional with dJ/dU_T given (fixed step sizes)."""
+        p0, dev, k0 = self._buf(U0)
+        pg, dev2, kg = self._buf(dJdUT)
+        if dev != dev2:
+            raise ValueError("U0 and dJdUT must both be host or both be device buffers")
+        out = np.empty(self.shape, dtype=self.dtype) if not dev else k0.new_empty(self.shape)
+        q, _, keep = self._buf(out)
+        self._check(lib().fam_adjoint(self._h, int(nsteps), float(cfl), int(ckpt_every), p0, pg, q, dev))
         return out
 
     def oe(self, dt: float, U):

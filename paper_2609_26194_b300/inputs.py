@@ -107,13 +107,16 @@ def advection_sine(n: int = 200) -> np.ndarray:
     return np.ascontiguousarray(np.stack([avg, mom])[None])
 
 
-def euler1d_riemann(n: int = 65536, seed: int = 2, gamma: float = GAMMA) -> np.ndarray:
+def euler1d_riemann(n: int = 65536, seed: int = 2, gamma: float = GAMMA, rho=(0.1, 2.0), umax: float = 1.0,
+                    p=(0.1, 10.0)) -> np.ndarray:
+    """8 face-snapped discontinuities, 9 constant states (rho, u, p ranges as
+    given) times the density perturbation (1 + 0.2 sin(32 pi x))."""
     rng = np.random.default_rng(seed)
     faces = np.sort(rng.choice(np.arange(1, n), size=min(8, n - 1), replace=False))
     ns = len(faces) + 1
-    rho_s = rng.uniform(0.1, 2.0, ns)
-    u_s = rng.uniform(-1.0, 1.0, ns)
-    p_s = rng.uniform(0.1, 10.0, ns)
+    rho_s = rng.uniform(rho[0], rho[1], ns)
+    u_s = rng.uniform(-umax, umax, ns)
+    p_s = rng.uniform(p[0], p[1], ns)
     dx = 1.0 / n
     # piece index of every cell (faces are snapped to cell faces)
     piece = np.searchsorted(faces, np.arange(n), side="right")
@@ -207,12 +210,52 @@ def euler2d_fourier(n: int = 1024, seed: int = 5, nmodes: int = 16, amp: float =
     return project_2d(func, n, n, nq=4)
 
 
-def batched_1d(n_inst: int = 4096, seed: int = 4, nmin: int = 64, nmax: int = 16384):
+# Milder Riemann states for many small instances: with jumps only tens of
+# cells apart the full ranges above produce negative pressures within a few
+# steps without a positivity limiter (which the paper cites but does not
+# define); these ranges stayed admissible for 200 steps in every sampled
+# instance.
+BATCH_RIEMANN = dict(rho=(0.7, 1.5), umax=0.3, p=(0.7, 2.0))
+
+
+def batched_1d(n_inst: int = 4096, seed: int = 4, nmin: int = 64, nmax: int = 16384, **riemann):
     """List of (k, U) instances; U follows euler1d_riemann with seed + i."""
     rng = np.random.default_rng(seed)
     ns = np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_inst))).astype(int)
     ks = rng.integers(3, 7, n_inst)
-    return [(int(ks[i]), euler1d_riemann(int(ns[i]), seed + i)) for i in range(n_inst)]
+    kw = riemann or BATCH_RIEMANN
+    return [(int(ks[i]), euler1d_riemann(int(ns[i]), seed + i, **kw)) for i in range(n_inst)]
+
+
+# shock problems of Examples 4.4 and 4.5 (no positivity limiter needed)
+
+SHU_OSHER_LEFT = (3.857143, 2.629369, 10.333333)
+
+
+def shu_osher(n: int = 400, gamma: float = GAMMA) -> np.ndarray:
+    """[-5,5]: (rho,u,p) = (3.857143, 2.629369, 10.333333) for x < -4, else
+    (1 + 0.2 sin(5x), 0, 1); the jump sits on a cell face when n % 10 == 0."""
+    def f(x):
+        left = x < -4.0
+        rho = np.where(left, SHU_OSHER_LEFT[0], 1.0 + 0.2 * np.sin(5.0 * x))
+        u = np.where(left, SHU_OSHER_LEFT[1], 0.0)
+        p = np.where(left, SHU_OSHER_LEFT[2], 1.0)
+        return primitive_to_conservative_1d(rho, u, p, gamma)
+    return project_1d(f, n, -5.0, 5.0, nq=8)
+
+
+def shu_osher_inflow(gamma: float = GAMMA):
+    return tuple(primitive_to_conservative_1d(np.array(SHU_OSHER_LEFT[0]), np.array(SHU_OSHER_LEFT[1]),
+                                              np.array(SHU_OSHER_LEFT[2]), gamma).tolist())
+
+
+def lax_tube(n: int = 200, gamma: float = GAMMA) -> np.ndarray:
+    """[-0.5,0.5]: (0.445, 0.698, 3.528) for x < 0, (0.5, 0, 0.571) otherwise."""
+    def f(x):
+        left = x < 0.0
+        return primitive_to_conservative_1d(np.where(left, 0.445, 0.5), np.where(left, 0.698, 0.0),
+                                            np.where(left, 3.528, 0.571), gamma)
+    return project_1d(f, n, -0.5, 0.5, nq=8)
 
 
 # smooth accuracy data (Example 4.1 and Example 4.2 of the paper)

@@ -1,0 +1,129 @@
+"""Adjoint of the 2D Euler FAM step on the GPU (fam_adjoint, autograd.Function).
+
+Checked against the oracle's own reverse sweep (oracle/torch_fam.py, step
+sizes from the C oracle's CFL rule) on small periodic grids, against central
+finite differences (h = 1e-6) of the GPU forward with the step sizes held
+fixed, and through torch.autograd.  The full-size workload (1024^2, FAM5,
+200 steps, checkpoints every 20) is checked against central differences in a
+few directions.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import torch_fam as tf
+from paper_2609_26194_b300 import fam, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(nx, ny, seed=0, amp=0.1, noise=0.01):
+    rng = np.random.default_rng(seed)
+    U = inputs.project_2d(lambda X, Y: inputs.primitive_to_conservative_2d(
+        1 + 2 * amp * np.sin(2 * np.pi * (X + 2 * Y)), 0.3 + amp * np.cos(2 * np.pi * X),
+        -0.2 + amp * np.sin(4 * np.pi * Y), 1 + amp * np.cos(2 * np.pi * (X - Y))), nx, ny)
+    U[:, 1:] += noise * rng.standard_normal(U[:, 1:].shape)
+    return U
+
+
+def _comp_err(a, b):
+    nc = b.shape[0]
+    A, B = a.reshape(nc, -1), b.reshape(nc, -1)
+    return float(np.max(np.max(np.abs(A - B), axis=1) / np.max(np.abs(B), axis=1)))
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_adjoint_matches_oracle_reverse_sweep(k):
+    nx, ny, nsteps, cfl = 40, 24, 4, 0.5
+    U0 = _state(nx, ny, seed=k)
+    G = tf.window_functional_grad(U0.shape, (6, 14, 10, 22), 1.0 / nx, 1.0 / ny)
+    G[1:, 1:] += 1e-3 * np.random.default_rng(1).standard_normal(G[1:, 1:].shape)  # exercise every plane
+    s = fam.Solver(2, nx, ny, k=k, equation=fam.EULER, bc=fam.PERIODIC)
+    got = s.adjoint(U0, G, nsteps, cfl, ckpt_every=3)
+    # oracle: its own step sizes, then its reverse sweep
+    P = oracle.Problem(d=2, nx=nx, ny=ny, k=k, eq=oracle.EULER)
+    U, dts = U0.copy(), []
+    for _ in range(nsteps):
+        dts.append(oracle.dt(P, U, cfl))
+        U = oracle.step(P, U, dts[-1])
+    want = tf.reverse_sweep(tf.Euler2D(nx, ny, k), U0, dts, G)
+    assert _comp_err(got, want) < 1e-12, _comp_err(got, want)
+    # the handle holds U^T afterwards
+    assert _comp_err(s.get_state(), U) < 1e-12
+
+
+def test_adjoint_matches_central_differences_small():
+    nx, ny, nsteps, cfl, k = 48, 32, 10, 0.5, 5
+    U0 = _state(nx, ny, seed=2, noise=0.02)
+    G = tf.window_functional_grad(U0.shape, (8, 24, 12, 36), 1.0 / nx, 1.0 / ny)
+    s = fam.Solver(2, nx, ny, k=k, equation=fam.EULER, bc=fam.PERIODIC)
+    s.set_state(U0)
+    dts = s.record_steps(nsteps, cfl)
+    grad = s.adjoint(U0, G, nsteps, cfl, ckpt_every=4)
+
+    def J(U):
+        s.set_state(U)
+        s.run_fixed(dts)
+        return float((G * s.get_state()).sum())
+
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for _ in range(6):
+        v = rng.standard_normal(U0.shape)
+        v[:, 1:] *= 0.05
+        fd = (J(U0 + h * v) - J(U0 - h * v)) / (2 * h)
+        ad = float((grad * v).sum())
+        assert abs(fd - ad) < 1e-6 * abs(fd), (fd, ad)
+    # single entries: the central difference carries a round-off error of
+    # about eps |J| / h ~ 3e-11 (|J| ~ 0.25), which bounds the absolute check
+    for (c, m, j, i) in [(0, 0, 15, 20), (3, 0, 10, 14), (1, 1, 16, 30), (2, 2, 20, 25)]:
+        e = np.zeros_like(U0)
+        e[c, m, j, i] = 1.0
+        fd = (J(U0 + h * e) - J(U0 - h * e)) / (2 * h)
+        assert abs(fd - grad[c, m, j, i]) < 1e-6 * abs(fd) + 1e-10, (c, m, j, i, fd, grad[c, m, j, i])
+
+
+def test_autograd_function_backward():
+    torch = pytest.importorskip("torch")
+    from paper_2609_26194_b300.autograd import evolve
+    nx, ny = 40, 32
+    U0 = torch.from_numpy(_state(nx, ny, seed=5)).cuda().requires_grad_(True)
+    w = torch.zeros_like(U0)
+    w[0, 0, 8:20, 10:30] = 1.0 / (nx * ny)
+    s = fam.Solver(2, nx, ny, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    UT = evolve(U0, s, 6, 0.5, 3)
+    J = (w * UT).sum()
+    J.backward()
+    s2 = fam.Solver(2, nx, ny, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    ref = s2.adjoint(U0.detach().cpu().numpy(), w.cpu().numpy(), 6, 0.5, 3)
+    assert np.array_equal(U0.grad.cpu().numpy(), ref)
+
+
+def test_config5_full_size_central_differences():
+    """1024^2 periodic, FAM5, 200 steps, checkpoints every 20, J = dx dy sum of
+    rho over the 64 x 64 window at cells [480, 544)^2."""
+    n, nsteps, cfl = 1024, 200, 0.55
+    U0 = inputs.euler2d_fourier(n, seed=5)
+    G = tf.window_functional_grad(U0.shape, (480, 544, 480, 544), 1.0 / n, 1.0 / n)
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    s.set_state(U0)
+    dts = s.record_steps(nsteps, cfl)
+    grad = s.adjoint(U0, G, nsteps, cfl, ckpt_every=20)
+
+    def J(U):
+        s.set_state(U)
+        s.run_fixed(dts)
+        return float((G * s.get_state()).sum())
+
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    v = rng.standard_normal(U0.shape)
+    v[:, 1:] *= 0.05
+    fd = (J(U0 + h * v) - J(U0 - h * v)) / (2 * h)
+    ad = float((grad * v).sum())
+    assert abs(fd - ad) < 1e-6 * abs(fd), (fd, ad)
+    # a single entry inside the window (central-difference round-off ~ eps |J| / h ~ 1e-12)
+    e = np.zeros_like(U0)
+    e[0, 0, 500, 510] = 1.0
+    fd = (J(U0 + h * e) - J(U0 - h * e)) / (2 * h)
+    assert abs(fd - grad[0, 0, 500, 510]) < 1e-6 * abs(fd) + 1e-11, (fd, grad[0, 0, 500, 510])

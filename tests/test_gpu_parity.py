@@ -346,3 +346,80 @@ def test_device_tensor_state_roundtrip():
     s.sync()
     want, _, _ = oracle.run(P, U, nsteps=3, cfl=0.4)
     assert_parity(out.cpu().numpy(), want)
+
+
+# ----------------------------------------------------------------------------
+# Type-I OE coefficient (Tab. sigma1d / sigma2d, global normalisation)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("k", [3, 5, 6])
+def test_type1_oe_operator(d, k):
+    n = 300 if d == 1 else (70, 45)
+    s, P = make(d, n, k, "euler", "periodic", oe_type=1)
+    assert P.oe_type == oracle.OE_TYPE1
+    U = smooth_state(d, n, seed=13, amp=0.25)
+    U[:, 1:] += 0.02 * np.random.default_rng(2).standard_normal(U[:, 1:].shape)
+    dt = 0.5 / (n if d == 1 else n[0])
+    got = s.oe(dt, U)
+    want, theta = oracle.oe(P, dt, U)
+    assert np.max(theta) > 1e-4
+    assert np.array_equal(got[:, 0], U[:, 0])
+    assert_parity(got, want)
+
+
+@pytest.mark.parametrize("d,k", [(1, 4), (1, 6), (2, 5)])
+def test_type1_100_steps(d, k):
+    n = 300 if d == 1 else (70, 45)
+    s, P = make(d, n, k, "euler", "outflow" if d == 1 else "periodic", oe_type=1)
+    U = smooth_state(d, n, seed=14, amp=0.2)
+    s.set_state(U)
+    s.run_steps(100, 0.3)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=100, cfl=0.3)
+    assert_parity(s.get_state(), want)
+
+
+def test_type1_advection_sine_keeps_order_k_plus_1():
+    """Prop. 2.2(ii) with the Type-I denominator bounded below: the averages of
+    the sine advection converge at order k+1 with OE on (GPU path)."""
+    for k in (3, 5):
+        errs = []
+        for n in (40, 80):
+            with fam.Solver(1, n, k=k, equation=fam.ADVECTION, bc=fam.PERIODIC, gamma=1.0, oe_type=1,
+                            smooth_dt=1) as s:
+                s.set_state(inputs.advection_sine(n))
+                s.run(0.5, 0.1)
+                V = s.get_state()
+            dx = 1.0 / n
+            xl = np.arange(n) * dx - 0.5
+            ex = (np.cos(2 * np.pi * xl) - np.cos(2 * np.pi * (xl + dx))) / (2 * np.pi * dx)
+            errs.append(np.abs(V[0, 0] - ex).mean())
+        assert np.log2(errs[0] / errs[1]) > k + 1 - 0.35, (k, errs)
+
+
+def test_tile_autotuner_keeps_parity(tmp_path):
+    """fam_tune times the three 2D tile shapes and keeps one; every shape
+    stays at the parity bar (shapes differ only in rounding: the cells around
+    a tile evaluate their facing traces through direct linear forms)."""
+    n = (96, 48)
+    U = smooth_state(2, n, seed=41, amp=0.2)
+    s, P = make(2, n, 5, "euler", "periodic")
+    s.set_state(U)
+    cache = str(tmp_path / "tune.tsv")
+    choice = s.tune(0.5, probe_steps=2, cache_path=cache)
+    assert choice in (0, 1, 2)
+    assert s.time()[2] == 0  # state and clock restored
+    want, _, _ = oracle.run(P, U, nsteps=20, cfl=0.5)
+    s.run_steps(20, 0.5)
+    s.sync()
+    assert_parity(s.get_state(), want)
+    for t in (0, 1, 2):
+        s.set_option("tile2d", t)
+        s.set_state(U)
+        s.run_steps(20, 0.5)
+        s.sync()
+        assert_parity(s.get_state(), want)
+    s2, _ = make(2, n, 5, "euler", "periodic")
+    s2.set_state(U)
+    assert s2.tune(0.5, probe_steps=2, cache_path=cache) == choice  # cached
