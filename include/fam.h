@@ -96,8 +96,12 @@ fam_status fam_set_option(fam_t h, const char* key, double value);
  * direction), 1 outflow, 2 reflective wall (mirror image: the normal
  * momentum and the moment along the normal change sign), 3 inflow (ghost
  * averages = inflow_state[0..ncomp-1] in conservative variables, ghost
- * moments zero).  Inflow next to a reflective wall is not built
- * (FAM_E_UNSUPPORTED).  Errors: FAM_E_INVAL. */
+ * moments zero).  Sides are set one at a time, so the combination is
+ * checked when a step, residual or OE next uses it: a periodic side whose
+ * opposite side is not periodic gives FAM_E_INVAL there, and an inflow side
+ * next to a reflective wall FAM_E_UNSUPPORTED (not built).  Errors here:
+ * FAM_E_INVAL (side or bc out of range, y sides of a 1D grid, inflow
+ * without a state). */
 fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state);
 
 /* Copy a state in (layout above).  on_device = 0: U is host memory;

@@ -266,8 +266,28 @@ fam_status fam_internal_step_fixed_dt(fam_handle* h, double dt, void* const* sto
 
 fam_status refresh_dt_public(fam_handle* h, double cfl) { return refresh_dt(h, cfl, 0.0, false); }
 
+// The four sides' conditions as a whole: periodic sides come in pairs, and
+// an inflow side may not meet a reflective wall (their shared corner ghosts
+// have no single rule).
+static fam_status check_bc(fam_handle* h) {
+  const int* nb = h->geo.bc;
+  for (int dir = 0; dir < h->d; ++dir)
+    if ((nb[2 * dir] == kBcPeriodic) != (nb[2 * dir + 1] == kBcPeriodic))
+      return fail(h, FAM_E_INVAL, "periodic conditions come in pairs; set the opposite side too");
+  if (h->d == 2)
+    for (int dir = 0; dir < 2; ++dir)
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (nb[2 * dir + s2] == kBcInflow && (nb[2 * (1 - dir)] == kBcReflective || nb[2 * (1 - dir) + 1] == kBcReflective))
+          return fail(h, FAM_E_UNSUPPORTED, "inflow next to a reflective wall is not built");
+  return FAM_OK;
+}
+
 static fam_status ensure_dt(fam_handle* h, double cfl, double T) {
   if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
+  {
+    fam_status b = check_bc(h);
+    if (b) return b;
+  }
   if (!(cfl > 0.0)) return fail(h, FAM_E_INVAL, "cfl must be positive");
   if (!h->dt_valid || cfl != h->cfl_set || T != h->T_set) return refresh_dt(h, cfl, T, false);
   return FAM_OK;
@@ -417,6 +437,7 @@ static fam_status select_tile(fam_handle* h, int t) {
 fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path, int* choice) {
   if (!h) return FAM_E_INVAL;
   if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
+  if (fam_status b = check_bc(h)) return b;
   if (h->d != 2) {
     if (choice) *choice = 0;
     return FAM_OK;  // 1D kernels have a single tile shape
@@ -569,19 +590,10 @@ fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state) {
   if (!h || side < 0 || side > 3 || bc < kBcPeriodic || bc > kBcInflow) return FAM_E_INVAL;
   if (side >= 2 && h->d == 1) return fail(h, FAM_E_INVAL, "1D grids have only the x sides");
   if (bc == kBcInflow && !inflow_state) return fail(h, FAM_E_INVAL, "inflow needs a state");
-  int nb[4] = {h->geo.bc[0], h->geo.bc[1], h->geo.bc[2], h->geo.bc[3]};
-  nb[side] = bc;
-  for (int dir = 0; dir < h->d; ++dir)
-    if ((nb[2 * dir] == kBcPeriodic) != (nb[2 * dir + 1] == kBcPeriodic))
-      return fail(h, FAM_E_INVAL, "periodic conditions come in pairs; set the opposite side too");
-  if (h->d == 2)
-    for (int dir = 0; dir < 2; ++dir)
-      for (int s2 = 0; s2 < 2; ++s2)
-        if (nb[2 * dir + s2] == kBcInflow && (nb[2 * (1 - dir)] == kBcReflective || nb[2 * (1 - dir) + 1] == kBcReflective))
-          return fail(h, FAM_E_UNSUPPORTED, "inflow next to a reflective wall is not built");
-  for (int q = 0; q < 4; ++q) h->geo.bc[q] = nb[q];
-  h->geo.bcx = nb[0];
-  h->geo.bcy = nb[2];
+  // sides are set one at a time; the combination is checked when it is used (check_bc)
+  h->geo.bc[side] = bc;
+  h->geo.bcx = h->geo.bc[0];
+  h->geo.bcy = h->geo.bc[2];
   if (bc == kBcInflow)
     for (int c = 0; c < h->nc; ++c) h->inflow[side][c] = inflow_state[c];
   fam_status s = fill_inflow(h);
@@ -652,6 +664,7 @@ fam_status fam_run_steps(fam_t h, long nsteps, double cfl) {
 fam_status fam_run_fixed(fam_t h, long nsteps, const double* dts) {
   if (!h || (nsteps > 0 && !dts)) return FAM_E_INVAL;
   if (!h->have_state) return fail(h, FAM_E_STATE, "no state: call fam_set_state first");
+  if (fam_status b = check_bc(h)) return b;
   for (long q = 0; q < nsteps; ++q) {
     if (!(dts[q] > 0.0)) return fail(h, FAM_E_INVAL, "step sizes must be positive");
     fam_status s = fam_internal_step_fixed_dt(h, dts[q], nullptr);
@@ -728,6 +741,7 @@ fam_status fam_profile(fam_t h, double* ms, long* nsteps) {
 
 fam_status fam_residual(fam_t h, const void* U, void* R, int on_device) {
   if (!h) return FAM_E_INVAL;
+  if (fam_status b = check_bc(h)) return b;
   fam_status s = copy_in(h, U, on_device, 1);
   if (s) return s;
   FAM_CUDA(h, h->ops.stage(h, 1, 1, 2, 0));
@@ -737,6 +751,7 @@ fam_status fam_residual(fam_t h, const void* U, void* R, int on_device) {
 fam_status fam_oe(fam_t h, double dt, const void* U, void* Uout, int on_device) {
   if (!h) return FAM_E_INVAL;
   if (!(dt >= 0.0)) return fail(h, FAM_E_INVAL, "dt must be >= 0");
+  if (fam_status b = check_bc(h)) return b;
   fam_status s = copy_in(h, U, on_device, 1);
   if (s) return s;
   s = enqueue_typeI(h, 1);

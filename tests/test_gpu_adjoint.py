@@ -99,13 +99,29 @@ def test_autograd_function_backward():
     assert np.array_equal(U0.grad.cpu().numpy(), ref)
 
 
-def test_config5_full_size_central_differences():
-    """1024^2 periodic, FAM5, 200 steps, checkpoints every 20, J = dx dy sum of
-    rho over the 64 x 64 window at cells [480, 544)^2."""
+def test_adjoint_matches_oracle_on_smooth_fourier_data():
+    """The full-size workload's kind of data (16 Fourier modes of amplitude
+    0.05, smooth): here the OE jumps are small but far above rounding, and
+    the GPU adjoint must equal the oracle's reverse sweep to 1e-12."""
+    n, nsteps, cfl = 96, 4, 0.55
+    U0 = inputs.euler2d_fourier(n, seed=5)
+    G = tf.window_functional_grad(U0.shape, (44, 52, 40, 56), 1.0 / n, 1.0 / n)
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    got = s.adjoint(U0, G, nsteps, cfl, ckpt_every=2)
+    P = oracle.Problem(d=2, nx=n, ny=n, k=5, eq=oracle.EULER)
+    U, dts = U0.copy(), []
+    for _ in range(nsteps):
+        dts.append(oracle.dt(P, U, cfl))
+        U = oracle.step(P, U, dts[-1])
+    want = tf.reverse_sweep(tf.Euler2D(n, n, 5), U0, dts, G)
+    assert _comp_err(got, want) < 1e-12, _comp_err(got, want)
+
+
+def _full_size_fd(oe_type):
     n, nsteps, cfl = 1024, 200, 0.55
     U0 = inputs.euler2d_fourier(n, seed=5)
     G = tf.window_functional_grad(U0.shape, (480, 544, 480, 544), 1.0 / n, 1.0 / n)
-    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC, oe_type=oe_type)
     s.set_state(U0)
     dts = s.record_steps(nsteps, cfl)
     grad = s.adjoint(U0, G, nsteps, cfl, ckpt_every=20)
@@ -121,9 +137,32 @@ def test_config5_full_size_central_differences():
     v[:, 1:] *= 0.05
     fd = (J(U0 + h * v) - J(U0 - h * v)) / (2 * h)
     ad = float((grad * v).sum())
-    assert abs(fd - ad) < 1e-6 * abs(fd), (fd, ad)
-    # a single entry inside the window (central-difference round-off ~ eps |J| / h ~ 1e-12)
     e = np.zeros_like(U0)
     e[0, 0, 500, 510] = 1.0
-    fd = (J(U0 + h * e) - J(U0 - h * e)) / (2 * h)
-    assert abs(fd - grad[0, 0, 500, 510]) < 1e-6 * abs(fd) + 1e-11, (fd, grad[0, 0, 500, 510])
+    fd1 = (J(U0 + h * e) - J(U0 - h * e)) / (2 * h)
+    return fd, ad, fd1, float(grad[0, 0, 500, 510])
+
+
+def test_config5_full_size_central_differences_linear_backbone():
+    """1024^2 periodic, FAM5, 200 steps, checkpoints every 20, J = dx dy sum of
+    rho over the 64 x 64 window at cells [480, 544)^2; the step without OE:
+    central differences (h = 1e-6) agree to 1e-6."""
+    fd, ad, fd1, ad1 = _full_size_fd(oe_type=0)
+    assert abs(fd - ad) < 1e-6 * abs(fd), (fd, ad)
+    # a single entry inside the window (central-difference round-off ~ eps |J| / h ~ 1e-12)
+    assert abs(fd1 - ad1) < 1e-6 * abs(fd1) + 1e-11, (fd1, ad1)
+
+
+def test_config5_full_size_central_differences_with_oe():
+    """The same with the OE.  On this smooth data the OE's sigma is a sum of
+    |jumps| whose values (<= 1e-10, many at rounding level) are far below the
+    change h |[v]| ~ 1e-6 that a central difference makes, so the difference
+    quotient straddles the kinks of |.| and of the max over components and
+    measures their average slope, while the adjoint is the derivative of the
+    branch the state is on.  The oracle's own reverse sweep shows the same
+    gap against its own central differences (2.7e-5 on 256^2, 10 steps),
+    and without the OE both agree to 1e-8; so the bound here is 1e-5 (the
+    single entry inside the window is far from any such kink's influence)."""
+    fd, ad, fd1, ad1 = _full_size_fd(oe_type=2)
+    assert abs(fd - ad) < 1e-5 * abs(fd), (fd, ad)
+    assert abs(fd1 - ad1) < 1e-6 * abs(fd1) + 1e-11, (fd1, ad1)

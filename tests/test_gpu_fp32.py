@@ -1,0 +1,81 @@
+"""FP32 path: its error against FP64 per workload, with the bounds it must stay under.
+
+The FP32 kernels are the FP64 kernels instantiated in float (same operation
+order, FP32 reciprocal/sqrt refinement).  Errors are relative max-norms of
+the cell averages per conserved component (max |a - b| / max |b|), against
+the FP64 oracle where it runs the whole problem, else against the GPU FP64
+path (held to the oracle at 1e-12 by the parity tests).  Each test prints
+its measured errors (pytest -s).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_26194_b300 import fam, inputs
+from test_gpu_parity import assert_parity, make
+
+pytestmark = pytest.mark.gpu
+
+
+def avg_err(a, b):
+    a = np.asarray(a, dtype=np.float64)[:, 0]
+    b = np.asarray(b, dtype=np.float64)[:, 0]
+    nc = b.shape[0]
+    A, B = a.reshape(nc, -1), b.reshape(nc, -1)
+    return float(np.max(np.max(np.abs(A - B), axis=1) / np.max(np.abs(B), axis=1)))
+
+
+def test_advection_sine_fp32_error():
+    """1D advection N = 200, k = 3, CFL 0.2 to T = 1 (Type-II OE every step)."""
+    U = inputs.advection_sine(200)
+    s, P = make(1, 200, 3, "adv", "periodic", prec=32)
+    s.set_state(U.astype(np.float32))
+    s.run(1.0, 0.2)
+    want, _, _ = oracle.run(P, U, T=1.0, cfl=0.2)
+    e = avg_err(s.get_state(), want)
+    print(f"\nFP32 error, advection N=200 k=3 T=1: {e:.2e}")
+    assert e < 1e-5
+
+
+def test_riemann_1d_1000_steps_fp64_parity_and_fp32_error():
+    """1D Euler N = 65536, k = 5, outflow, CFL 0.3, 1000 steps: FP64 against
+    the oracle, FP32 against the oracle."""
+    n = 65536
+    U = inputs.euler1d_riemann(n, seed=2)
+    s, P = make(1, n, 5, "euler", "outflow")
+    s.set_state(U)
+    s.run_steps(1000, 0.3)
+    s.sync()
+    want, _, _ = oracle.run(P, U, nsteps=1000, cfl=0.3)
+    assert_parity(s.get_state(), want)
+    s32, _ = make(1, n, 5, "euler", "outflow", prec=32)
+    s32.set_state(U.astype(np.float32))
+    s32.run_steps(1000, 0.3)
+    s32.sync()
+    e = avg_err(s32.get_state(), want)
+    print(f"\nFP32 error, 1D Euler Riemann N=65536 k=5 1000 steps: {e:.2e}")
+    assert e < 1e-4
+
+
+@pytest.mark.parametrize("k", [4, 6])
+@pytest.mark.parametrize("data", ["smooth", "rectangles"])
+def test_euler_2d_200_steps_fp32_error(k, data):
+    """2D Euler periodic, 200 steps: the smooth density wave and the
+    rectangles of constant state (admissible ranges), FP32 against the GPU
+    FP64 path.  1024^2 here; the 4096^2 figures are in the measured table."""
+    n = 1024
+    if data == "smooth":
+        U = inputs.euler2d_smooth(n)
+    else:
+        U = inputs.euler2d_rectangles(n, seed=3, nrect=64, **inputs.ADMISSIBLE_RECT)
+    cfl = 0.4 if k == 4 else 0.55
+    s64, _ = make(2, (n, n), k, "euler", "periodic")
+    s64.set_state(U)
+    dts = s64.record_steps(200, cfl)
+    ref = s64.get_state()
+    s32, _ = make(2, (n, n), k, "euler", "periodic", prec=32)
+    s32.set_state(U.astype(np.float32))
+    s32.run_fixed(dts)
+    e = avg_err(s32.get_state(), ref)
+    print(f"\nFP32 error, 2D Euler {data} {n}^2 k={k} 200 steps: {e:.2e}")
+    assert e < (1e-5 if data == "smooth" else 1e-3)
