@@ -38,15 +38,17 @@ METRIC = "2D Euler k=5 cell-stage updates/s"
 UNIT = "cell-stage/s"
 
 # Algorithmic FP64 work per cell and stage of the stage kernel: the executed
-# DFMA / DADD / DMUL instructions of one launch (ncu, 2048^2 FAM5; see
-# profiles/stage2d_k5_f64.md) per cell -- 1139 DFMA + 426 DADD + 511 DMUL =
-# 3215 FLOP with a DFMA counted as 2 -- minus the ~200 FLOP per cell that the
-# ring of cells around each 32x8 tile spends recomputing face traces.
-FLOP_PER_CELL_STAGE = {(5, 64): 3015.0}
+# DFMA / DADD / DMUL instructions of one launch per cell (ncu, 2048^2 FAM5,
+# 16x8 tiles; profiles/stage2d_k5_f64_2048.md): 1105.6 DFMA + 445.2 DADD
+# + 437.0 DMUL = 3093.4 FLOP with a DFMA counted as 2, minus the 240 FLOP per
+# cell that the ring cells around each 16x8 tile spend recomputing face
+# traces (48 ring cells x 4 components x 160 FLOP / 128 cells).  The count
+# excludes the ring, so it does not depend on the tile shape.
+FLOP_PER_CELL_STAGE = {(5, 64): 2853.4}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
-# dram__bytes_write.sum from the same capture, 1.184 GB / 4.19 M cells);
+# dram__bytes_write.sum from the same capture, 1.1885 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
-DRAM_BYTES_PER_CELL = {(5, 64): 282.4}
+DRAM_BYTES_PER_CELL = {(5, 64): 283.4}
 
 
 def parse():
@@ -60,6 +62,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32])
     ap.add_argument("--cfl", type=float, default=None)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2"],
+                    help="2D tile shape: the autotuner's pick, or an index into fam.TILES_2D")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-plain report")
@@ -174,8 +178,7 @@ def run_reference(a):
         return 0
     steps, warm = a.steps, a.warmup
     # each step: one oracle step on a 256 x 256 sample of the workload
-    base, _ = oracle_rate(a, 0, steps=warm + steps)
-    _, times = oracle_rate(a, 0, steps=warm + steps)
+    base, times = oracle_rate(a, 0, steps=warm + steps)
     t = sum(times[warm:])
     val = 3.0 * 256 * 256 * steps / t
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
@@ -336,6 +339,13 @@ def run_fam(a):
                    stream=stream.cuda_stream)
     dev = torch.from_numpy(U).cuda()
     s.set_state(dev)
+    # the library's tile autotuner (a few probe steps per tile shape, untimed)
+    if a.tile == "auto":
+        tile = fam.TILES_2D[s.tune(cfl, probe_steps=2)]
+        s.set_state(dev)
+    else:
+        s.set_option("tile2d", int(a.tile))
+        tile = fam.TILES_2D[int(a.tile)]
     for _ in range(a.warmup):
         s.step(cfl)
     s.sync()
@@ -405,7 +415,8 @@ def run_fam(a):
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32",
             "data": "synthetic (seeded analytic initial data, exact moments)",
-            "config": {**workload_config(a), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": {**workload_config(a), "tile": list(tile),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "hbm_roofline": hbm_roof,
             "kernel_ms": {"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
                           "stage3": kern_ms[2] / max(1, prof_steps), "oe": oe_ms},

@@ -124,6 +124,11 @@ static fam_status encode_maps(fam_handle* h) {
       cuuint32_t es[3] = {1, 1, 1};
       r = enc(&h->tm[b], dt, 3, h->buf[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r == CUDA_SUCCESS) {
+        cuuint32_t box_u0[3] = {(cuuint32_t)h->ops.tx + 4, (cuuint32_t)h->ops.ty, (cuuint32_t)h->np};
+        r = enc(&h->tm_u0[b], dt, 3, h->buf[b], dims, strides, box_u0, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      }
     } else {
       cuuint64_t dims[2] = {(cuuint64_t)h->geo.px, (cuuint64_t)h->np};
       cuuint64_t strides[1] = {(cuuint64_t)h->geo.plane * h->elem};

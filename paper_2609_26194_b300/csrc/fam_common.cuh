@@ -83,12 +83,23 @@ __host__ __device__ inline long long cell_index(const Geo& g, int plane, int j, 
 // ---------------------------------------------------------------------------
 // reciprocal and reciprocal square root
 // ---------------------------------------------------------------------------
-// FP64: the FP32 hardware approximation (rcp.approx / rsqrt.approx, about
-// 23 correct bits) is refined by Newton-Raphson steps in FP64, each of which
-// doubles the number of correct bits (Newton's method for f(r) = 1/r - x and
-// f(r) = 1/r^2 - x; e.g. Markstein, IBM J. Res. Dev. 34 (1990)).  Two steps
-// give a result within a few units in the last place.  Inputs are assumed
-// to lie in the FP32 normal range (physical densities and pressures).
+// FP64: a seed from the FP32 hardware approximation (rcp.approx /
+// rsqrt.approx) is refined by one third-order step in FP64.  With the seed r
+// and its residual e (e = 1 - x r for 1/x, e = 1 - x r^2 for 1/sqrt(x)) the
+// exact values are r / (1 - e) and r / sqrt(1 - e); their series in e,
+// truncated after the quadratic term (a third-order Householder step),
+// r (1 + e + e^2) and r (1 + e/2 + 3 e^2 / 8), leave an error of order e^3.
+// The seed carries about 20 correct bits (|e| < 2^-19), so e^3 < 2^-57 and
+// the result is within about one unit in the last place.  sqrt(x) folds the
+// final product: x r (1 + e/2 + 3 e^2 / 8) with x r computed once.
+//
+// The seed never passes through the FP64 conversion unit (whose
+// conversions share the slow FP64 pipe): the FP32 argument is assembled
+// with integer operations from the sign, exponent and leading 20 mantissa
+// bits of x's high word, and the FP32 result is widened the same way.  The
+// seeds are exact for |x| in [2^-125, 2^126); outside that range (and for
+// x <= 0 in rsqrt / sqrt) the result is NaN, which the status word reports
+// as a non-finite state.
 
 __device__ __forceinline__ float rcp_approx_f32(float x) {
   float r;
@@ -101,26 +112,59 @@ __device__ __forceinline__ float rsqrt_approx_f32(float x) {
   return r;
 }
 
+// FP32 number with the sign, exponent and first 20 mantissa bits of the
+// double whose high word is hi (exponent rebias 1023 -> 127 done modulo 2^32).
+__device__ __forceinline__ float narrow_hi(unsigned hi) {
+  return __uint_as_float((((hi & 0x7FFFFFFFu) << 3) + 0x40000000u) | (hi & 0x80000000u));
+}
+// The double equal to the normal FP32 number f.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned hi = (((b & 0x7FFFFFFFu) >> 3) + 0x38000000u) | (b & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+// |x| in [2^-125, 2^126) (biased exponent in [898, 1148]), where the FP32
+// argument and result (1/x or 1/sqrt(x)) are normal; the sign is ignored
+// (abs) or must be positive (pos)
+__device__ __forceinline__ bool seed_range_abs(unsigned hi) {
+  return ((hi & 0x7FFFFFFFu) - 0x38200000u) < 0x0FB00000u;
+}
+__device__ __forceinline__ bool seed_range_pos(unsigned hi) { return (hi - 0x38200000u) < 0x0FB00000u; }
+__device__ __forceinline__ double nan_f64() { return __longlong_as_double(0x7FF8000000000000ll); }
+
+// Flip the sign of v where m has the (64-bit) sign mask set; integer-only.
+__device__ __forceinline__ double flip_sign(double v, unsigned long long m) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)m);
+}
+__device__ __forceinline__ float flip_sign(float v, unsigned long long m) {
+  return __uint_as_float(__float_as_uint(v) ^ (unsigned)(m >> 32));
+}
+
 template <typename T> struct Fast;
 
 template <> struct Fast<double> {
   static __device__ __forceinline__ double rcp(double x) {
-    double r = (double)rcp_approx_f32((float)x);
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+    const unsigned hi = (unsigned)__double2hiint(x);
+    double r = widen_f32(rcp_approx_f32(narrow_hi(hi)));
+    r = seed_range_abs(hi) ? r : nan_f64();
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
   }
   static __device__ __forceinline__ double rsqrt(double x) {
-    double r = (double)rsqrt_approx_f32((float)x);
-    double hr = 0.5 * r;
-    double e = fma(-x * r, r, 1.0);
-    r = fma(hr, e, r);
-    hr = 0.5 * r;
-    e = fma(-x * r, r, 1.0);
-    return fma(hr, e, r);
+    const unsigned hi = (unsigned)__double2hiint(x);
+    double r = widen_f32(rsqrt_approx_f32(narrow_hi(hi)));
+    r = seed_range_pos(hi) ? r : nan_f64();
+    const double e = fma(-x * r, r, 1.0);
+    return fma(r * e, fma(0.375, e, 0.5), r);
   }
-  static __device__ __forceinline__ double sqrt_(double x) { return x * rsqrt(x); }
+  static __device__ __forceinline__ double sqrt_(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    double r = widen_f32(rsqrt_approx_f32(narrow_hi(hi)));
+    r = seed_range_pos(hi) ? r : nan_f64();
+    const double xr = x * r;
+    const double e = fma(-xr, r, 1.0);
+    return fma(xr * e, fma(0.375, e, 0.5), xr);
+  }
   static __device__ __forceinline__ double exp_(double x) { return exp(x); }
 };
 

@@ -53,6 +53,7 @@ struct fam_handle {
   double* t1_partial = nullptr;  // Type-I OE block partial sums
   int t1_blocks = 0;
   CUtensorMap tm[3];
+  CUtensorMap tm_u0[3];  // 2D: U^n rows of a tile (box (tx+4) x ty x planes)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool have_state = false;
@@ -135,7 +136,7 @@ struct Impl2D {
   }
   static cudaError_t stage(fam_handle* h, int in, int u0, int out, int s) {
     stage2d<T, K, PH, TX2, TY2><<<grid(h), TX2 * TY2, S::bytes_stage, h->stream>>>(
-        h->tm[in], bufp<T>(h, u0), bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
+        h->tm[in], h->tm_u0[u0], bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
     return cudaGetLastError();
   }
   static cudaError_t oe(fam_handle* h, int in, int out, double dto) {

@@ -54,6 +54,13 @@ __device__ __forceinline__ int ghost_images(int i, int n, int lo, int hi, int sg
 // Write v to cell (i, j) of plane p and to every ghost image of that cell.
 template <typename T>
 __device__ __forceinline__ void store_with_ghosts(T* __restrict__ out, const Geo& g, int p, int j, int i, T v) {
+  // cells at least G away from every side have no image (the common case)
+  const bool near_x = i < G || i >= g.nx - G;
+  const bool near_y = g.rows > 1 && (j < G || j >= g.ny - G);
+  if (!(near_x || near_y)) {
+    out[cell_index(g, p, j, i)] = v;
+    return;
+  }
   int xs[4], xsg[4], ys[4], ysg[4];
   const int nxs = ghost_images(i, g.nx, g.bc[0], g.bc[1], reflect_sign(g, p, 0), xs, xsg);
   int nys = 1;
@@ -73,7 +80,11 @@ struct Smem2D {
   static constexpr int TILE = NP * HY * HX;
   static constexpr int XF = (TX + 1) * TY * 4 * NC;  // x-face slots
   static constexpr int YF = TX * (TY + 1) * 4 * NC;  // y-face slots
-  static constexpr size_t bytes_stage = sizeof(T) * (size_t)(TILE + 2 * XF + 2 * YF) + 16 + 64 * sizeof(double);
+  // stage kernel: tile, then U^n rows of the tile (x halo kept for TMA alignment)
+  static constexpr int U0OFF = (TILE + 31) / 32 * 32;
+  static constexpr int U0T = NP * TY * HX;
+  static constexpr size_t bytes_stage =
+      sizeof(T) * (size_t)(U0OFF + U0T + 2 * XF + 2 * YF) + 16 + 64 * sizeof(double);
   static constexpr size_t bytes_oe =
       sizeof(T) * (size_t)(TILE + 4 * NC * (TX + 2) * (TY + 2) + 2 * (TX + 2) * (TY + 2)) + 16 + 64 * sizeof(double);
 };
@@ -121,8 +132,8 @@ __device__ __forceinline__ void gather_patch(const T* tile, int c, int hx, int h
 // stage = 1, 2, 3: Shu--Osher stage; stage = 0: write the residual R only.
 template <typename T, int K, class PH, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, 1)
-    stage2d(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ U0, T* __restrict__ Uout,
-            const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
+    stage2d(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_u0,
+            T* __restrict__ Uout, const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
@@ -132,19 +143,33 @@ __global__ void __launch_bounds__(TX * TY, 1)
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
-  T* xL = tile + S::TILE;  // left-side trace of x-face, later the flux
+  T* u0s = tile + S::U0OFF;  // U^n on the tile's rows (stages 2, 3)
+  T* xL = u0s + S::U0T;      // left-side trace of x-face, later the flux
   T* xR = xL + S::XF;
-  T* yB = xR + S::XF;      // bottom-side trace of y-face, later the flux
+  T* yB = xR + S::XF;        // bottom-side trace of y-face, later the flux
   T* yT = yB + S::YF;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(yT + S::YF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(yT + S::YF);  // [0] tile, [1] U^n
 
   const double dtd = (stage == 0) ? 0.0 : ctl->dt;
   if (stage != 0 && !(dtd > 0.0)) return;  // run finished: keep the state
   const T dt = T(dtd);
 
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  if (threadIdx.x == 0) prefetch_tmap(&tm_in);
+  const bool want_u0 = stage >= 2;
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tm_in);
+    mbar_init(bar + 1, 1);
+    if (want_u0) {
+      prefetch_tmap(&tm_u0);
+      fence_mbar_init();
+    }
+  }
   if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
+  // U^n arrives while phases A and B run (box (TX+4) x TY x NP at padded (x0, y0+G))
+  if (want_u0 && threadIdx.x == 0) {
+    mbar_expect_tx(bar + 1, (uint32_t)(sizeof(T) * S::U0T));
+    tma_load_3d(u0s, &tm_u0, bar + 1, x0, y0 + G, 0);
+  }
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int hx = tx + 2, hy = ty + 2;
@@ -214,34 +239,50 @@ __global__ void __launch_bounds__(TX * TY, 1)
       yT[((ty * TX + tx) * 4 + g) * NC + c] = b[g];
     }
   }
-  // ring cells around the tile: only the trace facing the tile
-  for (int r = threadIdx.x; r < 2 * (TX + TY); r += NT) {
-    int rx, ry, kind;
-    if (r < TY) { rx = -1; ry = r; kind = 0; }                          // left: right trace
-    else if (r < 2 * TY) { rx = TX; ry = r - TY; kind = 1; }            // right: left trace
-    else if (r < 2 * TY + TX) { rx = r - 2 * TY; ry = -1; kind = 2; }   // bottom: top trace
-    else { rx = r - 2 * TY - TX; ry = TY; kind = 3; }                   // top: bottom trace
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T A[9], X[9], Y[9], t[4];
-      gather_patch<T, HX, HY>(tile, c, rx + 2, ry + 2, A, X, Y);
-      if (kind == 0) {
-        Recon2D<K>::tr_xp(A, X, Y, t);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) xL[((ry * (TX + 1) + 0) * 4 + g) * NC + c] = t[g];
-      } else if (kind == 1) {
-        Recon2D<K>::tr_xm(A, X, Y, t);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) xR[((ry * (TX + 1) + TX) * 4 + g) * NC + c] = t[g];
-      } else if (kind == 2) {
-        Recon2D<K>::tr_yp(A, X, Y, t);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) yB[((0 * TX + rx) * 4 + g) * NC + c] = t[g];
-      } else {
-        Recon2D<K>::tr_ym(A, X, Y, t);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) yT[((TY * TX + rx) * 4 + g) * NC + c] = t[g];
+  // Ring cells around the tile: only the trace facing the tile, one task per
+  // (ring cell, component).  The reconstruction commutes with the symmetries
+  // of the square stencil, so every task evaluates the right-face traces
+  // (tr_xp) of a mirrored / transposed patch:
+  //   left ring cell   needs tr_xp of u(x, y)               (identity)
+  //   right ring cell  needs tr_xm = tr_xp of u(-x, y)       (x-moments change sign)
+  //   bottom ring cell needs tr_yp = tr_xp of u(y, x)        (x- and y-moments swap)
+  //   top ring cell    needs tr_ym = tr_xp of u(y, -x)       (swap; new x-moment = -old y-moment)
+  // with the Gauss points in the same ascending order.  All lanes run one
+  // code path; only the gather offsets differ.
+  {
+    constexpr int NR = 2 * (TX + TY);
+    for (int task = threadIdx.x; task < NR * NC; task += NT) {
+      const int r = task % NR, c = task / NR;
+      int rx, ry, ox, oy, swap;
+      unsigned long long xsign;
+      T* out;
+      if (r < TY) {  // left column: its right trace = left side of x-face 0
+        rx = -1; ry = r; ox = 1; oy = HX; swap = 0; xsign = 0ull;
+        out = xL + (ry * (TX + 1) + 0) * 4 * NC;
+      } else if (r < 2 * TY) {  // right column: its left trace = right side of x-face TX
+        rx = TX; ry = r - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull;
+        out = xR + (ry * (TX + 1) + TX) * 4 * NC;
+      } else if (r < 2 * TY + TX) {  // bottom row: its top trace = bottom side of y-face 0
+        rx = r - 2 * TY; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull;
+        out = yB + (0 * TX + rx) * 4 * NC;
+      } else {  // top row: its bottom trace = top side of y-face TY
+        rx = r - 2 * TY - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull;
+        out = yT + (TY * TX + rx) * 4 * NC;
       }
+      const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + (ry + 2) * HX + (rx + 2);
+      const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * HY * HX + (ry + 2) * HX + (rx + 2);
+      const T* py = tile + (size_t)(c * 3 + (swap ? 1 : 2)) * HY * HX + (ry + 2) * HX + (rx + 2);
+      T A[9], X[9], Y[9], t[4];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int o = (q % 3 - 1) * ox + (q / 3 - 1) * oy;
+        A[q] = pa[o];
+        X[q] = flip_sign(px[o], xsign);
+        Y[q] = py[o];
+      }
+      Recon2D<K>::tr_xp(A, X, Y, t);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) out[g * NC + c] = t[g];
     }
   }
   __syncthreads();
@@ -268,14 +309,21 @@ __global__ void __launch_bounds__(TX * TY, 1)
       sL = ph.flux_y(uL, fL);
       sR = ph.flux_y(uR, fR);
     }
+    // twice the Rusanov flux, f^- + f^+ - alpha (u^+ - u^-); the factor 1/2
+    // is folded into the quadrature weights of phase C (exact: a power of 2)
     const T a = fmax(sL, sR);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) slot[c] = T(0.5) * (fL[c] + fR[c]) - T(0.5) * a * (uR[c] - uL[c]);
+    for (int c = 0; c < NC; ++c) slot[c] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
   }
   __syncthreads();
 
   // ---- phase C: residual (eq. 11), Shu--Osher combination, store ---------
   const int i = x0 + tx, j = y0 + ty;
+  if (want_u0 && !mbar_wait(bar + 1, 0)) {
+    atomicOr(&ctl->status, kStatusTimeout);
+    mbar_wait(bar + 1, 0);  // let an in-flight copy land before the block exits
+    return;
+  }
   if (i >= geo.nx || j >= geo.ny) return;
   const T idx_ = T(geo.idx), idy_ = T(geo.idy);
   T avg[NC];
@@ -285,7 +333,13 @@ __global__ void __launch_bounds__(TX * TY, 1)
   ph.vol_finish(VA, avg, V1, V2);
   double w0, w1;
   stage_weights(stage, w0, w1);
-  const T gx[4] = {T(famgen::kGaussX[0]), T(famgen::kGaussX[1]), T(famgen::kGaussX[2]), T(famgen::kGaussX[3])};
+  // half weights (the face slots hold twice the flux) and half weight x node
+  T hw[4], hwx[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    hw[g] = T(0.5 * famgen::kGaussW[g]);
+    hwx[g] = T(0.5 * famgen::kGaussW[g] * famgen::kGaussX[g]);
+  }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const T* fl = xL + ((ty * (TX + 1) + tx) * 4) * NC + c;
@@ -296,12 +350,12 @@ __global__ void __launch_bounds__(TX * TY, 1)
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const T a = fl[g * NC], b = fr[g * NC], cb = fb[g * NC], ct = ft[g * NC];
-      sxl = fma(wg[g], a, sxl);
-      sxr = fma(wg[g], b, sxr);
-      syb = fma(wg[g], cb, syb);
-      syt = fma(wg[g], ct, syt);
-      mx = fma(wg[g] * gx[g], b - a, mx);   // int eta (f_x(+1/2) - f_x(-1/2)) over the x-faces
-      my = fma(wg[g] * gx[g], ct - cb, my);
+      sxl = fma(hw[g], a, sxl);
+      sxr = fma(hw[g], b, sxr);
+      syb = fma(hw[g], cb, syb);
+      syt = fma(hw[g], ct, syt);
+      mx = fma(hwx[g], b - a, mx);   // int eta (f_x(+1/2) - f_x(-1/2)) over the x-faces
+      my = fma(hwx[g], ct - cb, my);
     }
     T R[3];
     R[0] = -(sxr - sxl) * idx_ - (syt - syb) * idy_;
@@ -318,7 +372,7 @@ __global__ void __launch_bounds__(TX * TY, 1)
         if (stage == 1) {
           v = us + dt * R[m];
         } else {
-          const T u0 = U0[cell_index(geo, p, j, i)];
+          const T u0 = u0s[(size_t)p * TY * HX + ty * HX + hx];
           v = T(w0) * u0 + T(w1) * (us + dt * R[m]);
         }
       }

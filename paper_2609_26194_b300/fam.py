@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libfam.so")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
 PERIODIC, OUTFLOW, REFLECTIVE, INFLOW = 0, 1, 2, 3
+# 2D tile shapes (cells per CTA in x, y) selectable with the "tile2d" option / tune()
+TILES_2D = ((32, 8), (32, 4), (16, 8))
 STATUS = {0: "FAM_OK", 1: "FAM_E_INVAL", 2: "FAM_E_NOMEM", 3: "FAM_E_CUDA", 4: "FAM_E_NONPHYSICAL",
           5: "FAM_E_TIMEOUT", 6: "FAM_E_STATE", 7: "FAM_E_UNSUPPORTED"}
 
@@ -188,7 +190,8 @@ class Solver:
         self._check(lib().fam_sync(self._h))
 
     def tune(self, cfl: float, probe_steps: int = 2, cache_path: str | None = None) -> int:
-        """Pick the fastest 2D tile shape on the current state (returns the index)."""
+        """Pick the fastest 2D tile shape on the current state; returns its
+        index into TILES_2D (the state and clock are restored)."""
         c = ctypes.c_int()
         self._check(lib().fam_tune(self._h, float(cfl), int(probe_steps),
                                    cache_path.encode() if cache_path else None, ctypes.byref(c)))

@@ -11,6 +11,8 @@ a per-plane relative bar of 1e-9, which any error in a formula would exceed
 by orders of magnitude.  Sizes span several tiles with ragged tails (1D:
 128-cell tiles; 2D: 32 x 8 tiles).
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -91,13 +93,25 @@ def smooth_state(d, n, seed=0, amp=0.1):
 # building blocks
 # ----------------------------------------------------------------------------
 
-def test_newton_reciprocal_and_sqrt_within_few_ulp():
+def test_reciprocal_and_sqrt_within_few_ulp():
+    """Third-order refinement of FP32 seeds: within a few ulp on the seed
+    range |x| in [2^-125, 2^126), NaN outside it (and for x <= 0 under a
+    square root), so that such states are reported as non-finite."""
     rng = np.random.default_rng(5)
-    x = np.exp(rng.uniform(np.log(1e-6), np.log(1e6), 200000))
+    x = np.exp(rng.uniform(np.log(1e-36), np.log(1e36), 200000))
+    x[:4] = [2.0 ** -125, 2.0 ** 126 * (1 - 2.0 ** -52), 1.0, 0.75]
     r, rs, sq = fam.selftest_math(x)
+    exact_r = np.array([float(Fraction(1) / Fraction(v)) for v in x[:2000]])
+    assert np.max(np.abs(r[:2000] / exact_r - 1.0)) < 2 * 2.2e-16
     assert np.max(np.abs(r * x - 1.0)) < 4 * 2.2e-16
     assert np.max(np.abs(rs / (1.0 / np.sqrt(x)) - 1.0)) < 4 * 2.2e-16
     assert np.max(np.abs(sq / np.sqrt(x) - 1.0)) < 4 * 2.2e-16
+    r, _, _ = fam.selftest_math(-x)
+    assert np.max(np.abs(r * -x - 1.0)) < 4 * 2.2e-16
+    bad = np.array([0.0, 1e-300, 2.0 ** -126, 2.0 ** 126, 1e300, -1.0, -1e-3])
+    r, rs, sq = fam.selftest_math(bad)
+    assert np.all(np.isnan(r[:5])) and np.all(np.isfinite(r[5:]))
+    assert np.all(np.isnan(rs)) and np.all(np.isnan(sq))
 
 
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
