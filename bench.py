@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-plain report")
     ap.add_argument("--batched-steps", type=int, default=500)
+    ap.add_argument("--batched2d-steps", type=int, default=50)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     return ap.parse_args()
 
@@ -260,6 +261,14 @@ def batched_report(a, torch):
         sv.close()
     bv = 3.0 * cells * a.batched_steps / batched_s
     pv = 3.0 * cells * plain_steps / plain_s
+    # algorithmic HBM traffic of 1D Euler FP64: 8 state passes of 48 B per
+    # cell per step = 128 B per cell-stage
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
     return {"workload": "4096 x 1D Euler, N log-uniform [64,16384], k in {3,4,5,6}, outflow, CFL 0.3, "
                         "Riemann data (rho [0.7,1.5], |u| <= 0.3, p [0.7,2]), FP64", "instances": len(nx),
             "cells": cells,
@@ -268,9 +277,73 @@ def batched_report(a, torch):
                        "blocks_per_sm": bps, "kernel_launches": 1},
             "plain_loop": {"value": pv, "unit": UNIT, "steps": plain_steps, "seconds": plain_s,
                            "kernel_launches": 4 * len(nx) * plain_steps},
+            "hbm_roofline": {"algorithmic_bytes_per_cell_stage": 128.0, "achieved_gbs": 128.0 * bv / 1e9,
+                             "peak_gbs": hbm, "frac": 128.0 * bv / 1e9 / hbm},
             "speedup_vs_plain": bv / pv, "all_instances_advanced": bool(np.all(steps == a.batched_steps)),
             "status": status,
             "dt_spread": [float(np.min(dts)), float(np.max(dts))]}
+
+
+def batched2d_report(a, torch):
+    """Many independent 2D Euler problems (1024 instances, nx, ny log-uniform
+    in [16, 256] -- 256 to 65536 cells, the cell-count spread of the 1D batch
+    -- k in {3..6}, periodic density waves) advanced 50 steps in one
+    persistent launch, against the plain per-instance step loop."""
+    from paper_2609_26194_b300 import fam, inputs
+    insts = inputs.batched_2d(1024, seed=6, nmin=16, nmax=256)
+    nx = [U.shape[-1] for _, U in insts]
+    ny = [U.shape[-2] for _, U in insts]
+    ks = [k for k, _ in insts]
+    cells = sum(x * y for x, y in zip(nx, ny))
+    cfl, nsteps = 0.4, a.batched2d_steps
+    b = fam.Batch(nx, ks, ny=ny, bc=fam.PERIODIC)
+    b.set_state([U for _, U in insts])
+    tx, bps = b.tune(cfl, probe_steps=2)
+    b.set_state([U for _, U in insts])
+    b.run(0, cfl)
+    b.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(nsteps, cfl)
+    status = "ok"
+    try:
+        b.sync()
+    except fam.FamError as e:
+        status = str(e)
+    batched_s = time.perf_counter() - t0
+    info = b.info()
+    _, dts, steps = b.times()
+    b.close()
+    plain_steps = 5
+    solvers = []
+    for (k, U), n, m in zip(insts, nx, ny):
+        sv = fam.Solver(2, n, m, k=k, equation=fam.EULER, bc=fam.PERIODIC,
+                        tile2d=fam.TILES_2D.index((info["tile_x"], info["tile_y"])))
+        sv.set_state(U)
+        sv.step(cfl)
+        solvers.append(sv)
+    for sv in solvers:
+        sv.sync()
+    t0 = time.perf_counter()
+    for _ in range(plain_steps):
+        for sv in solvers:
+            sv.step(cfl)
+    for sv in solvers:
+        sv.sync()
+    plain_s = time.perf_counter() - t0
+    for sv in solvers:
+        sv.close()
+    bv = 3.0 * cells * nsteps / batched_s
+    pv = 3.0 * cells * plain_steps / plain_s
+    return {"workload": "1024 x 2D Euler, nx, ny log-uniform [16,256], k in {3,4,5,6}, periodic, CFL 0.4, "
+                        "density waves (exact moments), FP64", "instances": len(nx), "cells": cells,
+            "steps": nsteps, "value": bv, "unit": UNIT, "seconds": batched_s,
+            "launch": {"tile": [info["tile_x"], info["tile_y"]], "grid_blocks": info["grid"],
+                       "tiles": info["tiles"], "blocks_per_sm": bps, "kernel_launches": 1},
+            "plain_loop": {"value": pv, "unit": UNIT, "steps": plain_steps, "seconds": plain_s,
+                           "kernel_launches": 4 * len(nx) * plain_steps},
+            "speedup_vs_plain": bv / pv, "all_instances_advanced": bool(np.all(steps == nsteps)),
+            "status": status}
 
 
 def adjoint_report(a, torch):
@@ -423,6 +496,7 @@ def run_fam(a):
             "e2e": e2e, "gpu_launches": 4 * a.steps, "clocks": ck}
     if rank == 0 and world == 1 and not a.no_batched:
         line["batched"] = batched_report(a, torch)
+        line["batched2d"] = batched2d_report(a, torch)
     if rank == 0 and world == 1 and not a.no_adjoint:
         line["adjoint"] = adjoint_report(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

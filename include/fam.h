@@ -190,22 +190,34 @@ fam_status fam_adjoint(fam_t h, long nsteps, double cfl, int ckpt_every, const v
                        void* dJdU0, int on_device);
 
 /* ------------------------------------------------------------------------
- * Batched 1D problems (not in the paper: many independent instances in one
- * persistent launch).  Instance i has nx[i] cells on [x0, x1] and order
- * k[i]; all share the equation, bc, gamma (see fam_create) and precision.
- * State layout: the instances' 1D states (U_i[c][m][i]) concatenated in
- * instance order.  Each instance takes its own CFL step size (Sec. 4) from
- * its own maximum Rusanov speed.  The per-tile arithmetic is the
- * single-problem code, so each instance evolves exactly as fam_step would.
+ * Batched problems (not in the paper: many independent instances in one
+ * persistent launch).
+ *
+ * 1D: instance i has nx[i] cells on [x0, x1] and order k[i]; all share the
+ * equation, bc (periodic or outflow), gamma (see fam_create) and precision.
+ * 2D (fam_batch2d_create; 2D Euler): instance i has nx[i] x ny[i] cells on
+ * [x0, x1] x [y0, y1] and order k[i].
+ * State layout: the instances' states (1D U_i[c][m][i], 2D U_i[c][m][j][i])
+ * concatenated in instance order.  Each instance takes its own CFL step
+ * size (Sec. 4) from its own maximum Rusanov speed(s).  The per-tile
+ * arithmetic is the single-problem code, so each instance evolves exactly
+ * as fam_step would (in 2D: with the same tile shape, option "tile2d").
+ * Type-I OE, inflow and reflective sides are not offered for batches.
  * ------------------------------------------------------------------------ */
 typedef struct fam_batch* fam_batch_t;
 
 /* Errors: FAM_E_INVAL (bad sizes/orders), FAM_E_NOMEM, FAM_E_CUDA. */
 fam_status fam_batch_create(fam_batch_t* out, int n_inst, const int* nx, const int* k, double x0, double x1,
                             int equation, int bc, double gamma, int precision, void* stream);
+/* 2D batch of the Euler equations (equation must be FAM_EULER, else
+ * FAM_E_UNSUPPORTED).  nx, ny, k: arrays of n_inst (each nx, ny >= 4). */
+fam_status fam_batch2d_create(fam_batch_t* out, int n_inst, const int* nx, const int* ny, const int* k, double x0,
+                              double x1, double y0, double y1, int equation, int bc, double gamma, int precision,
+                              void* stream);
 /* Keys: "oe_type" (0 / 2), "gamma_k" (<= 0: defaults per order), "ax",
- * "tile_x" (64 / 128 / 256 cells per tile), "blocks_per_sm" (<= 0: the
- * occupancy maximum). */
+ * "tile_x" (1D: 64 / 128 / 256 cells per tile), "tile2d" (2D: 0 / 1 / 2 for
+ * 32x8 / 32x4 / 16x8 cells per tile), "blocks_per_sm" (<= 0: the occupancy
+ * maximum). */
 fam_status fam_batch_set_option(fam_batch_t h, const char* key, double value);
 /* Copy the concatenated state in / out (on_device as in fam_set_state);
  * set_state resets every instance's clock. */
@@ -220,12 +232,16 @@ fam_status fam_batch_sync(fam_batch_t h);
 /* Per-instance time, next step size and steps taken (arrays of n_inst; any
  * may be NULL).  Synchronous. */
 fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps);
-/* Launch shape: tile width, blocks of the persistent grid, tiles, cells. */
+/* Launch shape: tile width (2D: the tile's x extent), blocks of the
+ * persistent grid, tiles, cells. */
 fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, long* cells);
-/* Autotuner: times probe_steps steps for each tile width (64, 128, 256) and
- * blocks-per-SM choice on the handle's current state (restored afterwards),
- * keeps the fastest, and appends it to cache_path (if not NULL) keyed by GPU
- * name and problem; a cached entry is reused without timing. */
+/* Tile extents in cells (1D: tile_y = 1).  Either pointer may be NULL. */
+fam_status fam_batch_tile(fam_batch_t h, int* tile_x, int* tile_y);
+/* Autotuner: times probe_steps steps for each tile shape (1D widths 64,
+ * 128, 256; 2D 32x8, 32x4, 16x8) and blocks-per-SM choice on the handle's
+ * current state (restored afterwards), keeps the fastest, and appends it to
+ * cache_path (if not NULL) keyed by GPU name and problem; a cached entry is
+ * reused without timing.  *tile_x receives the tile's x extent. */
 fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char* cache_path, int* tile_x,
                           int* blocks_per_sm);
 const char* fam_batch_last_error(fam_batch_t h);

@@ -38,6 +38,8 @@ def units():
     out = [("fam_api", os.path.join(CSRC, "fam_api.cu"), []),
            ("fam_probe", os.path.join(CSRC, "fam_probe.cu"), []),
            ("fam_batch", os.path.join(CSRC, "fam_batch.cu"), []),
+           ("fam_batch2d_p64", os.path.join(CSRC, "fam_batch2d.cu"), ["-DFAM_P=64"]),
+           ("fam_batch2d_p32", os.path.join(CSRC, "fam_batch2d.cu"), ["-DFAM_P=32"]),
            ("fam_noalloc", os.path.join(CSRC, "fam_noalloc.cu"), []),
            ("fam_adjoint2d", os.path.join(CSRC, "fam_adjoint2d.cu"), [])]
     for d in (1, 2):

@@ -405,8 +405,9 @@ __global__ void adj_oe_local(const T* __restrict__ U, const Geo geo, const PH ph
     pstar[c] = ps;
     sgnp[c] = (lam[c][ps] - S) >= T(0) ? T(1) : T(-1);
     act[c] = !(d < T(1e-14) * fmax(mabs, T(1)));
-    sxc[c] = act[c] ? gamma_k * (fabs(jx[c][0]) + fabs(jx[c][1])) / d : T(0);
-    syc[c] = act[c] ? gamma_k * (fabs(jy[c][0]) + fabs(jy[c][1])) / d : T(0);
+    const T gd = act[c] ? gamma_k * Fast<T>::rcp(d) : T(0);
+    sxc[c] = act[c] ? gd * (fabs(jx[c][0]) + fabs(jx[c][1])) : T(0);
+    syc[c] = act[c] ? gd * (fabs(jy[c][0]) + fabs(jy[c][1])) : T(0);
   }
   int lx = 0, ly = 0;
   T sx = T(0), sy = T(0);
@@ -454,17 +455,19 @@ __global__ void adj_oe_local(const T* __restrict__ U, const Geo geo, const PH ph
   for (int c = 0; c < NC; ++c) Db[c] = T(0);
   if (sx > T(0)) {
     const int c = lx;
-    const T k = sxb * gamma_k / Dn[c];
+    const T iD = Fast<T>::rcp(Dn[c]);
+    const T k = sxb * gamma_k * iD;
     jb[0][c] += k * (jx[c][0] > T(0) ? T(1) : (jx[c][0] < T(0) ? T(-1) : T(0)));
     jb[1][c] += k * (jx[c][1] > T(0) ? T(1) : (jx[c][1] < T(0) ? T(-1) : T(0)));
-    Db[c] -= sxb * sx / Dn[c];
+    Db[c] -= sxb * sx * iD;
   }
   if (sy > T(0)) {
     const int c = ly;
-    const T k = syb * gamma_k / Dn[c];
+    const T iD = Fast<T>::rcp(Dn[c]);
+    const T k = syb * gamma_k * iD;
     jb[2][c] += k * (jy[c][0] > T(0) ? T(1) : (jy[c][0] < T(0) ? T(-1) : T(0)));
     jb[3][c] += k * (jy[c][1] > T(0) ? T(1) : (jy[c][1] < T(0) ? T(-1) : T(0)));
-    Db[c] -= syb * sy / Dn[c];
+    Db[c] -= syb * sy * iD;
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {

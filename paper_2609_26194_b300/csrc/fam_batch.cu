@@ -1,17 +1,18 @@
-// fam_batch.cu -- many independent 1D FAM problems in one persistent launch.
+// fam_batch.cu -- many independent FAM problems in one persistent launch.
 //
-// Instances of uneven size N_i and order k_i (3..6) share three packed state
+// Instances of uneven size and order k_i (3..6) share three packed state
 // buffers (A state, B and C stage buffers; instance i at element offset
-// off_i, SoA planes of padded pitch px_i).  Their cells are cut into tiles of
-// TX cells; one cooperative persistent kernel walks the tile list for each
-// pass of a time step -- stage 1, 2, 3 (eq. 3 / 12) and OE (eq. 9 /
+// off_i, SoA planes of padded pitch px_i).  1D: their cells are cut into tiles
+// of TX cells; one cooperative persistent kernel (below) walks the tile list
+// for each pass of a time step -- stage 1, 2, 3 (eq. 3 / 12) and OE (eq. 9 /
 // 1dOE_system) -- with a bounded grid barrier between passes, and a per-
 // instance step-size pass (Sec. 4 CFL rule with the instance's own maximum
 // Rusanov speed) at the end of each step.  The arithmetic per tile is the
 // same device code as the single-problem kernels (stage1d_tile,
 // oe1d_tile), so every instance evolves bit for bit as it would alone.
+// 2D (Euler): the same scheme over TX x TY tiles, kernel in fam_batch2d.cu.
 //
-// Tile width and blocks per SM are chosen by fam_batch_tune(), which times
+// Tile shape and blocks per SM are chosen by fam_batch_tune(), which times
 // each candidate on the handle's own data and can cache the choice in a file.
 #include <cuda_runtime.h>
 
@@ -26,65 +27,12 @@
 #include <vector>
 
 #include "../../include/fam.h"
+#include "fam_batch.cuh"
 #include "fam_kernels1d.cuh"
 
 using namespace fam;
 
 namespace {
-
-struct BatchInst {
-  long long off;  // element offset of plane 0
-  int nx, px, k, pad;
-  double dx, idx;
-  double gamma_k;
-};
-
-struct BatchCtl {
-  double dt, t;
-  unsigned long long alpha_bits;
-  unsigned long long steps;
-};
-
-struct BatchGlobal {
-  unsigned int bar_count, bar_gen, abort, status;
-};
-
-
-// Grid-wide barrier of a cooperative launch, with a bounded wait: a block
-// that waits longer than kWaitLimitNs (or sees another block give up)
-// records a timeout and returns false so that the whole kernel exits.
-__device__ bool grid_barrier(BatchGlobal* g, unsigned int nblocks) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned int* vgen = &g->bar_gen;
-    volatile unsigned int* vab = &g->abort;
-    const unsigned int my = atomicAdd(&g->bar_gen, 0u);
-    __threadfence();
-    if (atomicAdd(&g->bar_count, 1u) == nblocks - 1) {
-      atomicExch(&g->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&g->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*vgen == my) {
-        if (*vab) { ok = 0; break; }
-        if (global_ns() - t0 > kWaitLimitNs) {
-          atomicExch(&g->abort, 1u);
-          atomicOr(&g->status, kStatusTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
-}
 
 template <typename T, int TX>
 __device__ __forceinline__ void load_tile_plain(T* tile, const T* __restrict__ in, const BatchInst& I, int np,
@@ -116,7 +64,7 @@ __device__ __forceinline__ Geo geo_of(const BatchInst& I, int bc) {
 
 template <typename T, class PH, int TX>
 __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict__ inst,
-                                                    const int2* __restrict__ tiles, int ntiles, int ninst,
+                                                    const int4* __restrict__ tiles, int ntiles, int ninst,
                                                     T* A, T* B, T* C, BatchCtl* ictl, BatchGlobal* g, const PH ph,
                                                     int nsteps, double cfl, int oe_type, int bc, int init) {
   constexpr int NC = PH::NC, NP = 2 * NC, HX = TX + 4;
@@ -128,7 +76,7 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
   if (init) {
     // speeds at the cell averages of A -> first step size of every instance
     for (int t = blockIdx.x; t < ntiles; t += nb) {
-      const int2 td = tiles[t];
+      const int4 td = tiles[t];
       const BatchInst I = inst[td.x];
       double m = 0.0;
       const int i = td.y + threadIdx.x;
@@ -157,7 +105,7 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
       const T* in = pass == 1 ? A : pass == 2 ? B : pass == 3 ? C : B;
       T* out = pass == 1 ? B : pass == 2 ? C : pass == 3 ? B : A;
       for (int t = blockIdx.x; t < ntiles; t += nb) {
-        const int2 td = tiles[t];
+        const int4 td = tiles[t];
         const BatchInst I = inst[td.x];
         const double dtd = ictl[td.x].dt;
         if (!(dtd > 0.0)) continue;
@@ -231,23 +179,50 @@ __global__ void fill_ghosts_batch(T* U, const BatchInst* inst, int ninst, int np
   }
 }
 
+template <typename T>
+__global__ void fill_ghosts_batch2d(T* U, const BatchInst* inst, int ninst, int np, int bc) {
+  for (int i = blockIdx.x; i < ninst; i += gridDim.x) {
+    const BatchInst I = inst[i];
+    Geo geo;
+    geo.nx = I.nx; geo.ny = I.ny; geo.px = I.px; geo.rows = I.rows; geo.plane = I.plane; geo.bcx = geo.bcy = bc;
+    for (int q = 0; q < 4; ++q) geo.bc[q] = bc;
+    geo.nm = 3;
+    geo.euler = 1;
+    geo.dx = I.dx; geo.dy = I.dy; geo.idx = I.idx; geo.idy = I.idy;
+    const long long n = (long long)np * I.nx * I.ny;
+    for (long long q = threadIdx.x; q < n; q += blockDim.x) {
+      const int c = (int)(q % I.nx);
+      const long long r = q / I.nx;
+      const int j = (int)(r % I.ny), p = (int)(r / I.ny);
+      const T v = U[I.off + cell_index(geo, p, j, c)];
+      store_with_ghosts(U + I.off, geo, p, j, c, v);
+    }
+  }
+}
+
+// 2D tile shapes, the same as the single-problem 2D kernels'
+constexpr int kBatchTile2D[3][2] = {{32, 8}, {32, 4}, {16, 8}};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct fam_batch {
+  int d = 1;       // 1 or 2
+  int tile2d = 2;  // 2D: index into kBatchTile2D
   int n = 0, eq = FAM_EULER, bc = FAM_BC_OUTFLOW, prec = 64, nc = 3, np = 6;
   double gamma = 1.4, ax = 1.0;
   double gamma_k = 0.0;
   int oe_type = 2;
   size_t elem = 8;
-  std::vector<int> nx, k;
+  std::vector<int> nx, ny, k;
   std::vector<BatchInst> hinst;
   long long total = 0;  // elements per buffer
   long long cells = 0;
   BatchInst* dinst = nullptr;
-  int2* dtiles = nullptr;
+  Geo* dgeo = nullptr;  // 2D: per-instance geometry for the tile code
+  int4* dtiles = nullptr;
   int ntiles = 0;
   int tile_x = 128;
   int blocks_per_sm = 0;  // 0: occupancy maximum
@@ -292,7 +267,7 @@ static cudaError_t launch_run(fam_batch* h, const PH& ph, long nsteps, double cf
   T* C = reinterpret_cast<T*>(h->buf[2]);
   int ntiles = h->ntiles, ninst = h->n, ns = (int)nsteps, oe = h->oe_type, bc = h->bc;
   const BatchInst* di = h->dinst;
-  const int2* dtl = h->dtiles;
+  const int4* dtl = h->dtiles;
   BatchCtl* ic = h->ictl;
   BatchGlobal* gl = h->glob;
   void* args[] = {(void*)&di, (void*)&dtl, (void*)&ntiles, (void*)&ninst, (void*)&A, (void*)&B, (void*)&C,
@@ -312,6 +287,12 @@ static cudaError_t launch_tx(fam_batch* h, const PH& ph, long nsteps, double cfl
 
 static cudaError_t launch(fam_batch* h, long nsteps, double cfl, int init, bool q = false, int* g = nullptr) {
   const double gm = h->gamma;
+  if (h->d == 2) {
+    Batch2DArgs a{h->dinst, h->dgeo, h->dtiles, h->ntiles, h->n, h->buf[0], h->buf[1], h->buf[2], h->ictl, h->glob,
+                  h->eq, gm, (int)nsteps, cfl, h->oe_type, h->bc, init};
+    return h->prec == 64 ? fam_batch2d_launch_p64(a, h->tile2d, h->blocks_per_sm, q, g, h->stream)
+                         : fam_batch2d_launch_p32(a, h->tile2d, h->blocks_per_sm, q, g, h->stream);
+  }
   if (h->prec == 64) {
     switch (h->eq) {
       case FAM_ADVECTION: return launch_tx<double>(h, Advection1D<double>{h->ax}, nsteps, cfl, init, q, g);
@@ -329,25 +310,42 @@ static cudaError_t launch(fam_batch* h, long nsteps, double cfl, int init, bool 
 }
 
 static fam_status build_tiles(fam_batch* h) {
-  std::vector<int2> tl;
+  std::vector<int4> tl;
   std::vector<int> order(h->n);
   for (int i = 0; i < h->n; ++i) order[i] = i;
   // costliest orders first so that every round of the block-cyclic walk has
   // tiles of similar cost
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->k[a] > h->k[b]; });
-  for (int i : order)
-    for (int x0 = 0; x0 < h->nx[i]; x0 += h->tile_x) tl.push_back(make_int2(i, x0));
+  if (h->d == 1) {
+    for (int i : order)
+      for (int x0 = 0; x0 < h->nx[i]; x0 += h->tile_x) tl.push_back(make_int4(i, x0, 0, 0));
+  } else {
+    const int tx = kBatchTile2D[h->tile2d][0], ty = kBatchTile2D[h->tile2d][1];
+    for (int i : order)
+      for (int y0 = 0; y0 < h->ny[i]; y0 += ty)
+        for (int x0 = 0; x0 < h->nx[i]; x0 += tx) tl.push_back(make_int4(i, x0, y0, 0));
+  }
   h->ntiles = (int)tl.size();
   if (h->dtiles) cudaFree(h->dtiles);
   h->dtiles = nullptr;
-  FAMB_CUDA(h, cudaMalloc(&h->dtiles, sizeof(int2) * tl.size()));
-  FAMB_CUDA(h, cudaMemcpy(h->dtiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice));
+  FAMB_CUDA(h, cudaMalloc(&h->dtiles, sizeof(int4) * tl.size()));
+  FAMB_CUDA(h, cudaMemcpy(h->dtiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice));
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   return FAM_OK;
 }
 
 static fam_status fill_ghosts(fam_batch* h, int b) {
+  if (h->d == 2) {
+    if (h->prec == 64)
+      fill_ghosts_batch2d<double><<<std::min(h->n, 4096), 256, 0, h->stream>>>(
+          reinterpret_cast<double*>(h->buf[b]), h->dinst, h->n, h->np, h->bc);
+    else
+      fill_ghosts_batch2d<float><<<std::min(h->n, 4096), 256, 0, h->stream>>>(
+          reinterpret_cast<float*>(h->buf[b]), h->dinst, h->n, h->np, h->bc);
+    FAMB_CUDA(h, cudaGetLastError());
+    return FAM_OK;
+  }
   if (h->prec == 64)
     fill_ghosts_batch<double, 256><<<std::min(h->n, 4096), 256, 0, h->stream>>>(
         reinterpret_cast<double*>(h->buf[b]), h->dinst, h->n, h->np, h->bc);
@@ -378,43 +376,54 @@ static fam_status ensure_init(fam_batch* h, double cfl) {
 
 extern "C" {
 
-fam_status fam_batch_create(fam_batch_t* out, int n_inst, const int* nx, const int* k, double x0, double x1,
-                            int equation, int bc, double gamma, int precision, void* stream) {
-  if (!out || !nx || !k || n_inst <= 0) return FAM_E_INVAL;
+static fam_status create_batch(fam_batch_t* out, int d, int n_inst, const int* nx, const int* ny, const int* k,
+                               double x0, double x1, double y0, double y1, int equation, int bc, double gamma,
+                               int precision, void* stream) {
+  if (!out || !nx || !k || n_inst <= 0 || (d == 2 && !ny)) return FAM_E_INVAL;
   *out = nullptr;
   if (equation < FAM_ADVECTION || equation > FAM_EULER) return FAM_E_INVAL;
+  if (d == 2 && equation != FAM_EULER) return FAM_E_UNSUPPORTED;
   if (bc != FAM_BC_PERIODIC && bc != FAM_BC_OUTFLOW) return FAM_E_INVAL;
   if (precision != 64 && precision != 32) return FAM_E_INVAL;
-  if (!(x1 > x0)) return FAM_E_INVAL;
+  if (!(x1 > x0) || (d == 2 && !(y1 > y0))) return FAM_E_INVAL;
   if (equation == FAM_EULER && !(gamma > 1.0)) return FAM_E_INVAL;
   for (int i = 0; i < n_inst; ++i)
-    if (nx[i] < 4 || k[i] < 3 || k[i] > 6) return FAM_E_INVAL;
+    if (nx[i] < 4 || (d == 2 && ny[i] < 4) || k[i] < 3 || k[i] > 6) return FAM_E_INVAL;
   const char* fault = std::getenv("FAM_FAULT_ALLOC");
   if (fault && fault[0] == '1') return FAM_E_NOMEM;
   fam_batch* h = new fam_batch();
+  h->d = d;
   h->n = n_inst;
   h->eq = equation;
   h->bc = bc;
   h->prec = precision;
   h->gamma = gamma;
   h->ax = equation == FAM_ADVECTION ? gamma : 1.0;
-  h->nc = equation == FAM_EULER ? 3 : 1;
-  h->np = 2 * h->nc;
+  h->nc = equation == FAM_EULER ? d + 2 : 1;
+  h->np = (d + 1) * h->nc;
   h->elem = precision == 64 ? 8 : 4;
   h->nx.assign(nx, nx + n_inst);
+  h->ny.assign(n_inst, 1);
+  if (d == 2) h->ny.assign(ny, ny + n_inst);
   h->k.assign(k, k + n_inst);
   long long off = 0;
   for (int i = 0; i < n_inst; ++i) {
     BatchInst I{};
     I.off = off;
     I.nx = nx[i];
+    I.ny = h->ny[i];
     I.px = ((nx[i] + 2 * G) + 3) / 4 * 4;
+    I.rows = d == 2 ? h->ny[i] + 2 * G : 1;
+    I.plane = (long long)I.px * I.rows;
     I.k = k[i];
     I.dx = (x1 - x0) / nx[i];
     I.idx = 1.0 / I.dx;
-    I.gamma_k = k[i] <= 4 ? 25.0 : 12.5;
-    off += (long long)I.px * h->np;
-    h->cells += nx[i];
+    I.dy = d == 2 ? (y1 - y0) / h->ny[i] : 1.0;
+    I.idy = 1.0 / I.dy;
+    // default OE coefficient gamma_k per order and dimension (Sec. 4)
+    I.gamma_k = k[i] <= 4 ? 25.0 : (d == 2 ? 15.0 : 12.5);
+    off += I.plane * h->np;
+    h->cells += (long long)nx[i] * h->ny[i];
     h->hinst.push_back(I);
   }
   h->total = off;
@@ -437,11 +446,46 @@ fam_status fam_batch_create(fam_batch_t* out, int n_inst, const int* nx, const i
   if (cudaMalloc(&h->glob, sizeof(BatchGlobal)) != cudaSuccess) return bail(FAM_E_NOMEM);
   if (cudaMemcpy(h->dinst, h->hinst.data(), sizeof(BatchInst) * n_inst, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(FAM_E_CUDA);
+  if (d == 2) {
+    std::vector<Geo> gv(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+      const BatchInst& I = h->hinst[i];
+      Geo& g = gv[i];
+      std::memset(&g, 0, sizeof(g));
+      g.nx = I.nx;
+      g.ny = I.ny;
+      g.px = I.px;
+      g.rows = I.rows;
+      g.plane = I.plane;
+      g.bcx = g.bcy = bc;
+      for (int q = 0; q < 4; ++q) g.bc[q] = bc;
+      g.dx = I.dx;
+      g.dy = I.dy;
+      g.idx = I.idx;
+      g.idy = I.idy;
+      g.nm = 3;
+      g.euler = 1;
+    }
+    if (cudaMalloc(&h->dgeo, sizeof(Geo) * n_inst) != cudaSuccess) return bail(FAM_E_NOMEM);
+    if (cudaMemcpy(h->dgeo, gv.data(), sizeof(Geo) * n_inst, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(FAM_E_CUDA);
+  }
   if (build_tiles(h) != FAM_OK) return bail(FAM_E_CUDA);
   if (reset_clock(h) != FAM_OK) return bail(FAM_E_CUDA);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FAM_E_CUDA);
   *out = h;
   return FAM_OK;
+}
+
+fam_status fam_batch_create(fam_batch_t* out, int n_inst, const int* nx, const int* k, double x0, double x1,
+                            int equation, int bc, double gamma, int precision, void* stream) {
+  return create_batch(out, 1, n_inst, nx, nullptr, k, x0, x1, 0.0, 1.0, equation, bc, gamma, precision, stream);
+}
+
+fam_status fam_batch2d_create(fam_batch_t* out, int n_inst, const int* nx, const int* ny, const int* k, double x0,
+                              double x1, double y0, double y1, int equation, int bc, double gamma, int precision,
+                              void* stream) {
+  return create_batch(out, 2, n_inst, nx, ny, k, x0, x1, y0, y1, equation, bc, gamma, precision, stream);
 }
 
 void fam_batch_destroy(fam_batch_t h) {
@@ -451,6 +495,7 @@ void fam_batch_destroy(fam_batch_t h) {
   for (int b = 0; b < 3; ++b)
     if (h->buf[b]) cudaFree(h->buf[b]);
   if (h->dinst) cudaFree(h->dinst);
+  if (h->dgeo) cudaFree(h->dgeo);
   if (h->dtiles) cudaFree(h->dtiles);
   if (h->ictl) cudaFree(h->ictl);
   if (h->glob) cudaFree(h->glob);
@@ -467,13 +512,21 @@ fam_status fam_batch_set_option(fam_batch_t h, const char* key, double v) {
     if (v != 0.0 && v != 2.0) return bfail(h, FAM_E_INVAL, "oe_type must be 0 or 2");
     h->oe_type = (int)v;
   } else if (k == "gamma_k") {
-    for (auto& I : h->hinst) I.gamma_k = v > 0.0 ? v : (I.k <= 4 ? 25.0 : 12.5);
+    for (auto& I : h->hinst) I.gamma_k = v > 0.0 ? v : (I.k <= 4 ? 25.0 : (h->d == 2 ? 15.0 : 12.5));
     FAMB_CUDA(h, cudaMemcpy(h->dinst, h->hinst.data(), sizeof(BatchInst) * h->n, cudaMemcpyHostToDevice));
   } else if (k == "ax") {
     h->ax = v;
   } else if (k == "tile_x") {
+    if (h->d != 1) return bfail(h, FAM_E_INVAL, "tile_x applies to 1D batches (2D: tile2d)");
     if (v != 64.0 && v != 128.0 && v != 256.0) return bfail(h, FAM_E_INVAL, "tile_x must be 64, 128 or 256");
     h->tile_x = (int)v;
+    h->dt_valid = false;
+    return build_tiles(h);
+  } else if (k == "tile2d") {
+    if (h->d != 2) return bfail(h, FAM_E_INVAL, "tile2d applies to 2D batches");
+    if (v != 0.0 && v != 1.0 && v != 2.0) return bfail(h, FAM_E_INVAL, "tile2d must be 0, 1 or 2");
+    h->tile2d = (int)v;
+    h->dt_valid = false;
     return build_tiles(h);
   } else if (k == "blocks_per_sm") {
     h->blocks_per_sm = (int)v;
@@ -489,6 +542,26 @@ fam_status fam_batch_set_option(fam_batch_t h, const char* key, double v) {
 static fam_status batch_copy(fam_batch* h, void* dst_user, const void* src_user, int on_device, int b, bool in) {
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
   long long uoff = 0;
+  if (h->d == 2) {
+    // per instance and plane: ny rows of nx cells, interior at padded (G, G)
+    for (int i = 0; i < h->n; ++i) {
+      const BatchInst& I = h->hinst[i];
+      const size_t row = (size_t)I.nx * h->elem;
+      for (int p = 0; p < h->np; ++p) {
+        char* dev = reinterpret_cast<char*>(h->buf[b]) +
+                    (size_t)(I.off + (long long)p * I.plane + (long long)G * I.px + G) * h->elem;
+        const size_t u = (size_t)(uoff + (long long)p * I.nx * I.ny) * h->elem;
+        if (in)
+          FAMB_CUDA(h, cudaMemcpy2DAsync(dev, (size_t)I.px * h->elem, reinterpret_cast<const char*>(src_user) + u, row,
+                                         row, I.ny, kind, h->stream));
+        else
+          FAMB_CUDA(h, cudaMemcpy2DAsync(reinterpret_cast<char*>(dst_user) + u, row, dev, (size_t)I.px * h->elem, row,
+                                         I.ny, kind, h->stream));
+      }
+      uoff += (long long)I.nx * I.ny * h->np;
+    }
+    return FAM_OK;
+  }
   for (int i = 0; i < h->n; ++i) {
     const BatchInst& I = h->hinst[i];
     const size_t row = (size_t)I.nx * h->elem;
@@ -591,7 +664,7 @@ fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, l
   if (!h) return FAM_E_INVAL;
   int g = 0;
   FAMB_CUDA(h, launch(h, 0, 1.0, 0, true, &g));
-  if (tile_x) *tile_x = h->tile_x;
+  if (tile_x) *tile_x = h->d == 2 ? kBatchTile2D[h->tile2d][0] : h->tile_x;
   if (grid) *grid = g;
   if (ntiles) *ntiles = h->ntiles;
   if (cells) *cells = h->cells;
@@ -609,7 +682,9 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
   std::ostringstream key;
-  key << prop.name << "|eq" << h->eq << "|p" << h->prec << "|n" << h->n << "|cells" << h->cells;
+  key << prop.name << "|d" << h->d << "|eq" << h->eq << "|p" << h->prec << "|n" << h->n << "|cells" << h->cells;
+  // candidate tile shapes: 1D tile widths, 2D indices into kBatchTile2D
+  auto& shape = h->d == 1 ? h->tile_x : h->tile2d;
   if (cache_path && cache_path[0]) {
     std::ifstream f(cache_path);
     std::string line;
@@ -618,12 +693,12 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
       std::string k;
       int tx = 0, bps = 0;
       if (std::getline(ls, k, '\t') && (ls >> tx >> bps) && k == key.str()) {
-        h->tile_x = tx;
+        shape = tx;
         h->blocks_per_sm = bps;
         fam_status s = build_tiles(h);
         if (s) return s;
         h->dt_valid = false;
-        if (tile_x_out) *tile_x_out = tx;
+        if (tile_x_out) *tile_x_out = h->d == 2 ? kBatchTile2D[h->tile2d][0] : h->tile_x;
         if (blocks_per_sm_out) *blocks_per_sm_out = bps;
         return FAM_OK;
       }
@@ -636,11 +711,11 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best_tx = h->tile_x, best_b = h->blocks_per_sm;
+  int best_tx = shape, best_b = h->blocks_per_sm;
   float best = 1e30f;
-  const int txs[3] = {64, 128, 256};
-  for (int tx : txs) {
-    h->tile_x = tx;
+  const int txs1[3] = {64, 128, 256}, txs2[3] = {0, 1, 2};
+  for (int tx : (h->d == 1 ? txs1 : txs2)) {
+    shape = tx;
     if (build_tiles(h) != FAM_OK) continue;
     int occ_grid = 0;
     h->blocks_per_sm = 0;
@@ -669,7 +744,7 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->tile_x = best_tx;
+  shape = best_tx;
   h->blocks_per_sm = best_b;
   fam_status s = build_tiles(h);
   FAMB_CUDA(h, cudaMemcpyAsync(h->buf[0], save, h->total * h->elem, cudaMemcpyDeviceToDevice, h->stream));
@@ -682,8 +757,15 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
     std::ofstream f(cache_path, std::ios::app);
     f << key.str() << '\t' << best_tx << ' ' << best_b << '\n';
   }
-  if (tile_x_out) *tile_x_out = best_tx;
+  if (tile_x_out) *tile_x_out = h->d == 2 ? kBatchTile2D[h->tile2d][0] : h->tile_x;
   if (blocks_per_sm_out) *blocks_per_sm_out = best_b;
+  return FAM_OK;
+}
+
+fam_status fam_batch_tile(fam_batch_t h, int* tile_x, int* tile_y) {
+  if (!h) return FAM_E_INVAL;
+  if (tile_x) *tile_x = h->d == 2 ? kBatchTile2D[h->tile2d][0] : h->tile_x;
+  if (tile_y) *tile_y = h->d == 2 ? kBatchTile2D[h->tile2d][1] : 1;
   return FAM_OK;
 }
 

@@ -140,6 +140,45 @@ __device__ __forceinline__ float flip_sign(float v, unsigned long long m) {
   return __uint_as_float(__float_as_uint(v) ^ (unsigned)(m >> 32));
 }
 
+// Max and |.| of values >= 0 through their bit patterns (non-negative IEEE
+// numbers order like their integer patterns; a NaN operand wins): integer
+// operations, off the FP64 pipe.
+__device__ __forceinline__ double abs_bits(double v) {
+  return __longlong_as_double(__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ float abs_bits(float v) { return __uint_as_float(__float_as_uint(v) & 0x7FFFFFFFu); }
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
+__device__ __forceinline__ float max_nonneg(float a, float b) {
+  const int ia = __float_as_int(a), ib = __float_as_int(b);
+  return __int_as_float(ia > ib ? ia : ib);
+}
+
+// Min / max of any two non-NaN values through order-preserving integer keys
+// (negative patterns have their magnitude bits flipped).
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFll));
+}
+__device__ __forceinline__ int order_key(float v) {
+  const int b = __float_as_int(v);
+  return b ^ ((b >> 31) & 0x7FFFFFFF);
+}
+__device__ __forceinline__ float from_order_key(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7FFFFFFF)); }
+template <typename T> __device__ __forceinline__ T min_ordered(T a, T b) {
+  const auto ka = order_key(a), kb = order_key(b);
+  return from_order_key(ka < kb ? ka : kb);
+}
+template <typename T> __device__ __forceinline__ T max_ordered(T a, T b) {
+  const auto ka = order_key(a), kb = order_key(b);
+  return from_order_key(ka > kb ? ka : kb);
+}
+
 template <typename T> struct Fast;
 
 template <> struct Fast<double> {

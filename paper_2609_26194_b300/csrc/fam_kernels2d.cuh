@@ -129,47 +129,52 @@ __device__ __forceinline__ void gather_patch(const T* tile, int c, int hx, int h
 // ---------------------------------------------------------------------------
 // stage kernel
 // ---------------------------------------------------------------------------
-// stage = 1, 2, 3: Shu--Osher stage; stage = 0: write the residual R only.
-template <typename T, int K, class PH, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 1)
-    stage2d(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_u0,
-            T* __restrict__ Uout, const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
+// U^n for phase C from the TMA box in shared memory (single-problem kernel):
+// ready() waits (bounded) for the copy started before phase A.
+template <typename T, int TX, int TY>
+struct U0FromSmem {
+  const T* u0s;
+  uint64_t* bar;
+  FamCtl* ctl;
+  bool want;
+  __device__ __forceinline__ bool ready() const {
+    if (want && !mbar_wait(bar, 0)) {
+      atomicOr(&ctl->status, kStatusTimeout);
+      mbar_wait(bar, 0);  // let an in-flight copy land before the block exits
+      return false;
+    }
+    return true;
+  }
+  __device__ __forceinline__ T u0(const Geo&, int p, int, int, int ty, int hx) const {
+    return u0s[(size_t)p * TY * (TX + 4) + ty * (TX + 4) + hx];
+  }
+};
+
+// U^n read from global memory at the cell (batched kernel).
+template <typename T>
+struct U0FromGlobal {
+  const T* __restrict__ U0;
+  __device__ __forceinline__ bool ready() const { return true; }
+  __device__ __forceinline__ T u0(const Geo& g, int p, int j, int i, int, int) const {
+    return U0[cell_index(g, p, j, i)];
+  }
+};
+
+// One SSP-RK3 stage (stage = 1, 2, 3) or the residual alone (stage = 0) on
+// the TX x TY tile at (x0, y0), whose cells and 2-cell halo of every plane
+// are in shared memory at `tile` (HY x HX per plane).  xL, xR, yB, yT are the
+// face-trace / flux slots of Smem2D.  u0src supplies U^n for stages 2 and 3
+// (ready() is called once by every thread before phase C).
+template <typename T, int K, class PH, int TX, int TY, class U0Src>
+__device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, T* xR, T* yB, T* yT,
+                                             T* __restrict__ Uout, const Geo& geo, const PH& ph, const int stage,
+                                             const T dt, const int x0, const int y0, const U0Src& u0src) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
-  constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
+  constexpr int HX = S::HX, HY = S::HY;
   constexpr int D = K - 1;
   constexpr int NCOEF = Recon2D<K>::NCOEF;
   constexpr int NT = TX * TY;
-
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);
-  T* u0s = tile + S::U0OFF;  // U^n on the tile's rows (stages 2, 3)
-  T* xL = u0s + S::U0T;      // left-side trace of x-face, later the flux
-  T* xR = xL + S::XF;
-  T* yB = xR + S::XF;        // bottom-side trace of y-face, later the flux
-  T* yT = yB + S::YF;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(yT + S::YF);  // [0] tile, [1] U^n
-
-  const double dtd = (stage == 0) ? 0.0 : ctl->dt;
-  if (stage != 0 && !(dtd > 0.0)) return;  // run finished: keep the state
-  const T dt = T(dtd);
-
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const bool want_u0 = stage >= 2;
-  if (threadIdx.x == 0) {
-    prefetch_tmap(&tm_in);
-    mbar_init(bar + 1, 1);
-    if (want_u0) {
-      prefetch_tmap(&tm_u0);
-      fence_mbar_init();
-    }
-  }
-  if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
-  // U^n arrives while phases A and B run (box (TX+4) x TY x NP at padded (x0, y0+G))
-  if (want_u0 && threadIdx.x == 0) {
-    mbar_expect_tx(bar + 1, (uint32_t)(sizeof(T) * S::U0T));
-    tma_load_3d(u0s, &tm_u0, bar + 1, x0, y0 + G, 0);
-  }
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int hx = tx + 2, hy = ty + 2;
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(TX * TY, 1)
     }
     // twice the Rusanov flux, f^- + f^+ - alpha (u^+ - u^-); the factor 1/2
     // is folded into the quadrature weights of phase C (exact: a power of 2)
-    const T a = fmax(sL, sR);
+    const T a = max_nonneg(sL, sR);  // a NaN speed (non-physical trace) propagates
 #pragma unroll
     for (int c = 0; c < NC; ++c) slot[c] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
   }
@@ -319,11 +324,7 @@ __global__ void __launch_bounds__(TX * TY, 1)
 
   // ---- phase C: residual (eq. 11), Shu--Osher combination, store ---------
   const int i = x0 + tx, j = y0 + ty;
-  if (want_u0 && !mbar_wait(bar + 1, 0)) {
-    atomicOr(&ctl->status, kStatusTimeout);
-    mbar_wait(bar + 1, 0);  // let an in-flight copy land before the block exits
-    return;
-  }
+  if (!u0src.ready()) return;
   if (i >= geo.nx || j >= geo.ny) return;
   const T idx_ = T(geo.idx), idy_ = T(geo.idy);
   T avg[NC];
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(TX * TY, 1)
         if (stage == 1) {
           v = us + dt * R[m];
         } else {
-          const T u0 = u0s[(size_t)p * TY * HX + ty * HX + hx];
+          const T u0 = u0src.u0(geo, p, j, i, ty, hx);
           v = T(w0) * u0 + T(w1) * (us + dt * R[m]);
         }
       }
@@ -381,9 +382,198 @@ __global__ void __launch_bounds__(TX * TY, 1)
   }
 }
 
+
+// stage = 1, 2, 3: Shu--Osher stage; stage = 0: write the residual R only.
+template <typename T, int K, class PH, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 1)
+    stage2d(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_u0,
+            T* __restrict__ Uout, const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
+  constexpr int NC = PH::NC;
+  using S = Smem2D<T, NC, TX, TY>;
+  constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* u0s = tile + S::U0OFF;  // U^n on the tile's rows (stages 2, 3)
+  T* xL = u0s + S::U0T;      // left-side trace of x-face, later the flux
+  T* xR = xL + S::XF;
+  T* yB = xR + S::XF;        // bottom-side trace of y-face, later the flux
+  T* yT = yB + S::YF;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(yT + S::YF);  // [0] tile, [1] U^n
+
+  const double dtd = (stage == 0) ? 0.0 : ctl->dt;
+  if (stage != 0 && !(dtd > 0.0)) return;  // run finished: keep the state
+  const T dt = T(dtd);
+
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const bool want_u0 = stage >= 2;
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tm_in);
+    mbar_init(bar + 1, 1);
+    if (want_u0) {
+      prefetch_tmap(&tm_u0);
+      fence_mbar_init();
+    }
+  }
+  if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
+  // U^n arrives while phases A and B run (box (TX+4) x TY x NP at padded (x0, y0+G))
+  if (want_u0 && threadIdx.x == 0) {
+    mbar_expect_tx(bar + 1, (uint32_t)(sizeof(T) * S::U0T));
+    tma_load_3d(u0s, &tm_u0, bar + 1, x0, y0 + G, 0);
+  }
+
+  const U0FromSmem<T, TX, TY> u0src{u0s, bar + 1, ctl, want_u0};
+  stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, dt, x0, y0, u0src);
+}
+
 // ---------------------------------------------------------------------------
 // OE kernel (+ wave-speed reduction for the next step)
 // ---------------------------------------------------------------------------
+// The OE step (eq. 2dOE_sol / 2dOE_system, Tab. sigma2d) on the TX x TY tile
+// at (x0, y0) whose cells and 2-cell halo are in shared memory at `tile`;
+// fc and sp are the face-centre trace and speed scratch of Smem2D.  Type I
+// reads its global statistics from t1.  Returns, per thread, the Rusanov
+// speeds at its cell's average (0 outside the grid) for the next step size.
+template <typename T, int K, class PH, int TX, int TY>
+__device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* sp, T* __restrict__ Uout,
+                                          const Geo& geo, const PH& ph, const int oe_type, const T gamma_k,
+                                          const int q6, const T dt_idx, const T dt_idy, const int x0,
+                                          const int y0, const FamCtl* t1, unsigned int* status,
+                                          double& my_speed_x, double& my_speed_y) {
+  constexpr int NC = PH::NC;
+  using S = Smem2D<T, NC, TX, TY>;
+  constexpr int HX = S::HX, HY = S::HY;
+  constexpr int NT = TX * TY;
+  constexpr int RX = TX + 2, RY = TY + 2;  // tile plus one ring
+
+  // Face-centre traces (Tab. sigma2d jumps need the two traces at each face
+  // centre): all four of every tile cell, one task per (cell, component);
+  // the one trace each ring cell shows the tile, evaluated as the right-face
+  // trace of a mirrored / transposed patch (as in stage2d); the Rusanov
+  // speeds at the averages of the tile and its ring (corners included).
+  constexpr int NR = 2 * (TX + TY);
+  for (int task = threadIdx.x; task < TX * TY * NC; task += NT) {
+    const int cell = task % (TX * TY), c = task / (TX * TY);
+    const int cx = cell % TX, cy = cell / TX;
+    const int q = (cy + 1) * RX + (cx + 1);
+    T A[9], X[9], Y[9], t[4];
+    gather_patch<T, HX, HY>(tile, c, cx + 2, cy + 2, A, X, Y);
+    Recon2D<K>::facec(A, X, Y, t, q6);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) fc[(q * 4 + f) * NC + c] = t[f];
+  }
+  for (int task = threadIdx.x; task < NR * NC; task += NT) {
+    const int r = task % NR, c = task / NR;
+    int rx, ry, ox, oy, swap, slot;
+    unsigned long long xsign;
+    if (r < TY) {  // left ring column: its right trace
+      rx = -1; ry = r; ox = 1; oy = HX; swap = 0; xsign = 0ull; slot = 1;
+    } else if (r < 2 * TY) {  // right ring column: its left trace
+      rx = TX; ry = r - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; slot = 0;
+    } else if (r < 2 * TY + TX) {  // bottom ring row: its top trace
+      rx = r - 2 * TY; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; slot = 3;
+    } else {  // top ring row: its bottom trace
+      rx = r - 2 * TY - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; slot = 2;
+    }
+    const int off = (ry + 2) * HX + (rx + 2);
+    const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + off;
+    const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * HY * HX + off;
+    const T* py = tile + (size_t)(c * 3 + (swap ? 1 : 2)) * HY * HX + off;
+    T A[9], X[9], Y[9], t[4];
+#pragma unroll
+    for (int s2 = 0; s2 < 9; ++s2) {
+      const int o = (s2 % 3 - 1) * ox + (s2 / 3 - 1) * oy;
+      A[s2] = pa[o];
+      X[s2] = flip_sign(px[o], xsign);
+      Y[s2] = py[o];
+    }
+    Recon2D<K>::facec(A, X, Y, t, q6);  // only t[1] (x = +1/2) is used
+    const int q = (ry + 1) * RX + (rx + 1);
+    fc[(q * 4 + slot) * NC + c] = t[1];
+  }
+  for (int q = threadIdx.x; q < RX * RY; q += NT) {
+    const int hx = q % RX + 1, hy = q / RX + 1;
+    T u[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) u[c] = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
+    T sx, sy;
+    ph.speeds(u, sx, sy);
+    sp[q] = sx;
+    sp[RX * RY + q] = sy;
+  }
+  __syncthreads();
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool inside = i < geo.nx && j < geo.ny;
+  my_speed_x = 0.0;
+  my_speed_y = 0.0;
+  if (inside) {
+    const int rx = tx + 1, ry = ty + 1, q = ry * RX + rx;
+    const int hx = tx + 2, hy = ty + 2;
+    T sig_x = T(0), sig_y = T(0);
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      // jumps [[u]] = u(right/top side) - u(left/bottom side) at the four face centres
+      const T jxl = fc[(q * 4 + 0) * NC + c] - fc[((q - 1) * 4 + 1) * NC + c];
+      const T jxr = fc[((q + 1) * 4 + 0) * NC + c] - fc[(q * 4 + 1) * NC + c];
+      const T jyb = fc[(q * 4 + 2) * NC + c] - fc[((q - RX) * 4 + 3) * NC + c];
+      const T jyt = fc[((q + RX) * 4 + 2) * NC + c] - fc[(q * 4 + 3) * NC + c];
+      // Type II over the 3x3 stencil: S = sum of the averages (unnormalised,
+      // as printed), D = max |u_s - S| = max(S - min u, max u - S) (rounding
+      // is monotone, so this equals the max of the nine rounded differences)
+      const T* pa = tile + (size_t)(c * 3) * HY * HX;
+      T S = T(0), vmin, vmax;
+#pragma unroll
+      for (int s = 0; s < 9; ++s) {
+        const T v = pa[(hy + s / 3 - 1) * HX + (hx + s % 3 - 1)];
+        S += v;
+        vmin = s == 0 ? v : min_ordered(vmin, v);
+        vmax = s == 0 ? v : max_ordered(vmax, v);
+      }
+      T Dn = T(0), eps;
+      if (oe_type == 1) {
+        Dn = T(__longlong_as_double((long long)t1->t1_dev_bits[c]));
+        eps = T(1e-14) * max_nonneg(T(__longlong_as_double((long long)t1->t1_maxabs_bits[c])), T(1));
+      } else {
+        Dn = max_nonneg(S - vmin, vmax - S);  // one of the two is >= 0
+        eps = T(1e-14) * max_nonneg(max_nonneg(abs_bits(vmin), abs_bits(vmax)), T(1));
+      }
+      if (oe_type != 0 && !(Dn < eps)) {
+        const T g = gamma_k * Fast<T>::rcp(Dn);
+        sig_x = max_nonneg(sig_x, g * (fabs(jxl) + fabs(jxr)));
+        sig_y = max_nonneg(sig_y, g * (fabs(jyb) + fabs(jyt)));
+      }
+    }
+    T bx = T(0), by = T(0);
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+      const int qq = (ry + s / 3 - 1) * RX + (rx + s % 3 - 1);
+      bx = max_nonneg(bx, sp[qq]);
+      by = max_nonneg(by, sp[RX * RY + qq]);
+    }
+    const T theta = fma(bx * sig_x, dt_idx, by * sig_y * dt_idy);
+    const T delta = Fast<T>::exp_(-theta);
+    T uavg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T a = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
+      uavg[c] = a;
+      const T m1 = tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx] * delta;
+      const T m2 = tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx] * delta;
+      if (!isfinite(a) || !isfinite(m1) || !isfinite(m2)) ok = false;
+      store_with_ghosts(Uout, geo, c * 3 + 0, j, i, a);
+      store_with_ghosts(Uout, geo, c * 3 + 1, j, i, m1);
+      store_with_ghosts(Uout, geo, c * 3 + 2, j, i, m2);
+    }
+    if (!ok) atomicOr(status, kStatusNonFinite);
+    else if (!ph.admissible(uavg)) atomicOr(status, kStatusNonPhysical);
+    my_speed_x = (double)sp[q];
+    my_speed_y = (double)sp[RX * RY + q];
+  }
+}
+
 template <typename T, int K, class PH, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, 1)
     oe2d(const __grid_constant__ CUtensorMap tm_in, T* __restrict__ Uout, const Geo geo, const PH ph,
@@ -404,101 +594,15 @@ __global__ void __launch_bounds__(TX * TY, 1)
   const double dtd = dt_override >= 0.0 ? dt_override : ctl->dt;
   const bool reduce = dt_override < 0.0;
   if (!(dtd > 0.0) && reduce) return;
-  const T dt = T(dtd);
+  const T dt_idx = T(dtd * geo.idx), dt_idy = T(dtd * geo.idy);
 
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
 
-  // traces at face centres and speeds at averages for the tile and its ring
-  for (int q = threadIdx.x; q < RX * RY; q += NT) {
-    const int rx = q % RX, ry = q / RX;  // ring coordinates: cell (x0 + rx - 1, y0 + ry - 1)
-    const int hx = rx + 1, hy = ry + 1;
-    const bool corner = (rx == 0 || rx == RX - 1) && (ry == 0 || ry == RY - 1);
-    T u[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      u[c] = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
-      if (!corner) {
-        T A[9], X[9], Y[9], t[4];
-        gather_patch<T, HX, HY>(tile, c, hx, hy, A, X, Y);
-        Recon2D<K>::facec(A, X, Y, t, q6);
-#pragma unroll
-        for (int f = 0; f < 4; ++f) fc[(q * 4 + f) * NC + c] = t[f];
-      }
-    }
-    T sx, sy;
-    ph.speeds(u, sx, sy);
-    sp[q] = sx;
-    sp[RX * RY + q] = sy;
-  }
-  __syncthreads();
-
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i = x0 + tx, j = y0 + ty;
-  const bool inside = i < geo.nx && j < geo.ny;
-  double my_speed_x = 0.0, my_speed_y = 0.0;
-  if (inside) {
-    const int rx = tx + 1, ry = ty + 1, q = ry * RX + rx;
-    const int hx = tx + 2, hy = ty + 2;
-    T sig_x = T(0), sig_y = T(0);
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      // jumps [[u]] = u(right/top side) - u(left/bottom side) at the four face centres
-      const T jxl = fc[(q * 4 + 0) * NC + c] - fc[((q - 1) * 4 + 1) * NC + c];
-      const T jxr = fc[((q + 1) * 4 + 0) * NC + c] - fc[(q * 4 + 1) * NC + c];
-      const T jyb = fc[(q * 4 + 2) * NC + c] - fc[((q - RX) * 4 + 3) * NC + c];
-      const T jyt = fc[((q + RX) * 4 + 2) * NC + c] - fc[(q * 4 + 3) * NC + c];
-      const T* pa = tile + (size_t)(c * 3) * HY * HX;
-      T v[9], S = T(0), mabs = T(0);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        v[s] = pa[(hy + s / 3 - 1) * HX + (hx + s % 3 - 1)];
-        S += v[s];
-        mabs = fmax(mabs, fabs(v[s]));
-      }
-      T Dn = T(0), eps;
-      if (oe_type == 1) {
-        Dn = T(__longlong_as_double((long long)ctl->t1_dev_bits[c]));
-        eps = T(1e-14) * fmax(T(__longlong_as_double((long long)ctl->t1_maxabs_bits[c])), T(1));
-      } else {
-#pragma unroll
-        for (int s = 0; s < 9; ++s) Dn = fmax(Dn, fabs(v[s] - S));
-        eps = T(1e-14) * fmax(mabs, T(1));
-      }
-      if (oe_type != 0 && !(Dn < eps)) {
-        const T g = gamma_k * Fast<T>::rcp(Dn);
-        sig_x = fmax(sig_x, g * (fabs(jxl) + fabs(jxr)));
-        sig_y = fmax(sig_y, g * (fabs(jyb) + fabs(jyt)));
-      }
-    }
-    T bx = T(0), by = T(0);
-#pragma unroll
-    for (int s = 0; s < 9; ++s) {
-      const int qq = (ry + s / 3 - 1) * RX + (rx + s % 3 - 1);
-      bx = fmax(bx, sp[qq]);
-      by = fmax(by, sp[RX * RY + qq]);
-    }
-    const T theta = bx * dt * sig_x * T(geo.idx) + by * dt * sig_y * T(geo.idy);
-    const T delta = Fast<T>::exp_(-theta);
-    T uavg[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const T a = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
-      uavg[c] = a;
-      const T m1 = tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx] * delta;
-      const T m2 = tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx] * delta;
-      if (!isfinite(a) || !isfinite(m1) || !isfinite(m2)) ok = false;
-      store_with_ghosts(Uout, geo, c * 3 + 0, j, i, a);
-      store_with_ghosts(Uout, geo, c * 3 + 1, j, i, m1);
-      store_with_ghosts(Uout, geo, c * 3 + 2, j, i, m2);
-    }
-    if (!ok) atomicOr(&ctl->status, kStatusNonFinite);
-    else if (!ph.admissible(uavg)) atomicOr(&ctl->status, kStatusNonPhysical);
-    my_speed_x = (double)sp[q];
-    my_speed_y = (double)sp[RX * RY + q];
-  }
+  double my_speed_x, my_speed_y;
+  oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, dt_idx, dt_idy, x0, y0, ctl,
+                              &ctl->status, my_speed_x, my_speed_y);
   if (!reduce) return;
   const double mx = block_max<NT>(my_speed_x, red);
   const double my = block_max<NT>(my_speed_y, red + 32);

@@ -172,7 +172,7 @@ template <typename T> struct Euler2D {
   // ---- derivatives for the adjoint ------------------------------------------
   // ub += (d f_dir / d u)^T w  (flux Jacobian-transpose product)
   __device__ __forceinline__ void flux_vjp(int dir, const T* u, const T* w, T* ub) const {
-    const T r = T(1) / u[0];
+    const T r = Fast<T>::rcp(u[0]);
     const T vx = u[1] * r, vy = u[2] * r;
     const T q2 = vx * vx + vy * vy;
     const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
@@ -191,14 +191,14 @@ template <typename T> struct Euler2D {
   }
   // spectral radius |v_dir| + c and its gradient with respect to u
   __device__ __forceinline__ T speed_grad(int dir, const T* u, T* gr) const {
-    const T r = T(1) / u[0];
+    const T r = Fast<T>::rcp(u[0]);
     const T vx = u[1] * r, vy = u[2] * r;
     const T q2 = vx * vx + vy * vy;
     const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
-    const T c = sqrt(g * p * r);
+    const T c = Fast<T>::sqrt_(g * p * r);
     const T vn = dir == 0 ? vx : vy;
     const T sg = vn > T(0) ? T(1) : (vn < T(0) ? T(-1) : T(0));
-    const T kc = g / (T(2) * c * u[0]);   // dc = kc (dp - (p/rho) drho)
+    const T kc = T(0.5) * g * r * Fast<T>::rcp(c);   // dc = kc (dp - (p/rho) drho), kc = g / (2 c rho)
     // dp/du = gm1 (q2/2, -vx, -vy, 1); dvn/du = (-vn/rho, [dir==0]/rho, [dir==1]/rho, 0)
     gr[0] = -sg * vn * r + kc * (hgm1 * q2 - p * r);
     gr[1] = (dir == 0 ? sg * r : T(0)) - kc * gm1 * vx;

@@ -30,7 +30,8 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_status_string", "fam_destroy", "fam_alu_peak", "fam_selftest_math",
            "fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
            "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
-           "fam_batch_last_error", "fam_batch_destroy", "fam_step1d_noalloc", "fam_adjoint",
+           "fam_batch_last_error", "fam_batch_destroy", "fam_batch2d_create", "fam_batch_tile",
+           "fam_step1d_noalloc", "fam_adjoint",
            "fam_run_fixed", "fam_set_bc", "fam_tune")
 
 
@@ -267,16 +268,25 @@ def selftest_math(x: np.ndarray):
 
 
 class Batch:
-    """Many independent 1D problems advanced in one persistent launch (fam_batch_t)."""
+    """Many independent problems advanced in one persistent launch (fam_batch_t).
+
+    1D: Batch(nx, k, ...) -- instance i has nx[i] cells on [x0, x1].
+    2D (Euler): Batch(nx, k, ny=ny, ...) -- instance i has nx[i] x ny[i]
+    cells on [x0, x1] x [y0, y1].  States are lists of per-instance arrays of
+    shape (ncomp, 2, nx) or (4, 3, ny, nx)."""
 
     def __init__(self, nx, k, x0: float = 0.0, x1: float = 1.0, equation: int = EULER, bc: int = OUTFLOW,
-                 gamma: float = 1.4, precision: int = 64, stream: int | None = None):
+                 gamma: float = 1.4, precision: int = 64, stream: int | None = None, ny=None,
+                 y0: float = 0.0, y1: float = 1.0):
         self.nx = [int(v) for v in nx]
         self.k = [int(v) for v in k]
-        if len(self.nx) != len(self.k):
-            raise ValueError("nx and k must have the same length")
+        self.d = 1 if ny is None else 2
+        self.ny = [1] * len(self.nx) if ny is None else [int(v) for v in ny]
+        if len(self.nx) != len(self.k) or len(self.ny) != len(self.nx):
+            raise ValueError("nx, ny and k must have the same length")
         self.n = len(self.nx)
-        self.ncomp = 3 if equation == EULER else 1
+        self.ncomp = (self.d + 2) if equation == EULER else 1
+        self.nmom = self.d + 1
         self.precision = precision
         self.dtype = np.float64 if precision == 64 else np.float32
         L = lib()
@@ -284,11 +294,21 @@ class Batch:
         h = ctypes.c_void_p()
         anx = (ctypes.c_int * self.n)(*self.nx)
         ak = (ctypes.c_int * self.n)(*self.k)
-        rc = L.fam_batch_create(ctypes.byref(h), self.n, anx, ak, x0, x1, equation, bc, gamma, precision,
-                                ctypes.c_void_p(stream or 0))
+        if self.d == 1:
+            rc = L.fam_batch_create(ctypes.byref(h), self.n, anx, ak, x0, x1, equation, bc, gamma, precision,
+                                    ctypes.c_void_p(stream or 0))
+        else:
+            any_ = (ctypes.c_int * self.n)(*self.ny)
+            rc = L.fam_batch2d_create(ctypes.byref(h), self.n, anx, any_, ak, x0, x1, y0, y1, equation, bc, gamma,
+                                      precision, ctypes.c_void_p(stream or 0))
         if rc != 0:
             raise FamError(rc, "fam_batch_create failed")
         self._h = h
+
+    def _shape(self, i: int) -> tuple:
+        if self.d == 1:
+            return (self.ncomp, 2, self.nx[i])
+        return (self.ncomp, 3, self.ny[i], self.nx[i])
 
     def _check(self, rc):
         if rc != 0:
@@ -310,18 +330,19 @@ class Batch:
 
     def pack(self, states) -> np.ndarray:
         parts = []
-        for U, n in zip(states, self.nx):
+        for i, U in enumerate(states):
             U = np.ascontiguousarray(U, dtype=self.dtype)
-            if U.shape != (self.ncomp, 2, n):
-                raise ValueError(f"instance state shape {U.shape} != {(self.ncomp, 2, n)}")
+            if U.shape != self._shape(i):
+                raise ValueError(f"instance state shape {U.shape} != {self._shape(i)}")
             parts.append(U.reshape(-1))
         return np.ascontiguousarray(np.concatenate(parts))
 
     def unpack(self, flat) -> list:
         out, o = [], 0
-        for n in self.nx:
-            m = self.ncomp * 2 * n
-            out.append(flat[o:o + m].reshape(self.ncomp, 2, n))
+        for i in range(self.n):
+            shp = self._shape(i)
+            m = int(np.prod(shp))
+            out.append(flat[o:o + m].reshape(shp))
             o += m
         return out
 
@@ -330,7 +351,7 @@ class Batch:
         self._check(lib().fam_batch_set_state(self._h, ctypes.c_void_p(flat.ctypes.data), 0))
 
     def get_state(self) -> list:
-        flat = np.empty(sum(self.ncomp * 2 * n for n in self.nx), dtype=self.dtype)
+        flat = np.empty(sum(int(np.prod(self._shape(i))) for i in range(self.n)), dtype=self.dtype)
         self._check(lib().fam_batch_get_state(self._h, ctypes.c_void_p(flat.ctypes.data), 0))
         return self.unpack(flat)
 
@@ -352,7 +373,9 @@ class Batch:
         tx, g, nt, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_long(), ctypes.c_long()
         self._check(lib().fam_batch_info(self._h, ctypes.byref(tx), ctypes.byref(g), ctypes.byref(nt),
                                          ctypes.byref(nc)))
-        return {"tile_x": tx.value, "grid": g.value, "tiles": nt.value, "cells": nc.value}
+        ty = ctypes.c_int()
+        self._check(lib().fam_batch_tile(self._h, ctypes.byref(tx), ctypes.byref(ty)))
+        return {"tile_x": tx.value, "tile_y": ty.value, "grid": g.value, "tiles": nt.value, "cells": nc.value}
 
     def tune(self, cfl: float, probe_steps: int = 3, cache_path: str | None = None) -> tuple[int, int]:
         tx, b = ctypes.c_int(), ctypes.c_int()
@@ -372,6 +395,8 @@ def _batch_sigs(L):
     vp, dp, i, d, l = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_long
     ip = ctypes.POINTER(ctypes.c_int)
     L.fam_batch_create.argtypes = [ctypes.POINTER(vp), i, ip, ip, d, d, i, i, d, i, vp]
+    L.fam_batch2d_create.argtypes = [ctypes.POINTER(vp), i, ip, ip, ip, d, d, d, d, i, i, d, i, vp]
+    L.fam_batch_tile.argtypes = [vp, ip, ip]
     L.fam_batch_set_option.argtypes = [vp, ctypes.c_char_p, d]
     L.fam_batch_set_state.argtypes = [vp, vp, i]
     L.fam_batch_get_state.argtypes = [vp, vp, i]
@@ -384,8 +409,9 @@ def _batch_sigs(L):
     L.fam_batch_last_error.restype = ctypes.c_char_p
     L.fam_batch_destroy.argtypes = [vp]
     L.fam_batch_destroy.restype = None
-    for name in ("fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
-                 "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune"):
+    for name in ("fam_batch_create", "fam_batch2d_create", "fam_batch_set_option", "fam_batch_set_state",
+                 "fam_batch_get_state", "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info",
+                 "fam_batch_tune", "fam_batch_tile"):
         getattr(L, name).restype = ctypes.c_int
     _batch_ready = True
 

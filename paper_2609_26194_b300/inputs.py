@@ -227,6 +227,40 @@ def batched_1d(n_inst: int = 4096, seed: int = 4, nmin: int = 64, nmax: int = 16
     return [(int(ks[i]), euler1d_riemann(int(ns[i]), seed + i, **kw)) for i in range(n_inst)]
 
 
+def density_wave_2d(nx: int, ny: int, mx_: int, my_: int, phase: float, amp: float, u: float, v: float,
+                    p: float, gamma: float = GAMMA) -> np.ndarray:
+    """Periodic [0,1]^2 state rho = 1 + amp sin(2 pi (mx x + my y) + phase)
+    with constant u, v, p, on nx x ny cells (separable, exact moments)."""
+    Asx, Msx, Acx, Mcx = _sincos_moments(nx, 0.0, 1.0, 2.0 * np.pi * mx_, phase)
+    Asy, Msy, Acy, Mcy = _sincos_moments(ny, 0.0, 1.0, 2.0 * np.pi * my_)
+    avg = 1.0 + amp * (Asx[None, :] * Acy[:, None] + Acx[None, :] * Asy[:, None])
+    mx = amp * (Msx[None, :] * Acy[:, None] + Mcx[None, :] * Asy[:, None])
+    my = amp * (Asx[None, :] * Mcy[:, None] + Acx[None, :] * Msy[:, None])
+    rho = np.stack([avg, mx, my])
+    E = 0.5 * (u * u + v * v) * rho
+    E[0] += p / (gamma - 1.0)
+    return np.ascontiguousarray(np.stack([rho, u * rho, v * rho, E]))
+
+
+def batched_2d(n_inst: int = 256, seed: int = 6, nmin: int = 32, nmax: int = 512) -> list:
+    """List of (k, U) 2D Euler instances on [0,1]^2: nx, ny log-uniform in
+    [nmin, nmax] (independently), k uniform in {3..6}, a density wave with
+    wavenumbers in 1..3 and amplitude in [0.05, 0.2], u, v in [-0.5, 0.5],
+    p in [0.7, 1.5] (density_wave_2d)."""
+    rng = np.random.default_rng(seed)
+    nxs = np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_inst))).astype(int)
+    nys = np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_inst))).astype(int)
+    ks = rng.integers(3, 7, n_inst)
+    out = []
+    for i in range(n_inst):
+        m1, m2 = (int(v) for v in rng.integers(1, 4, 2))
+        ph, a = rng.uniform(0, 2 * np.pi), rng.uniform(0.05, 0.2)
+        u, v = rng.uniform(-0.5, 0.5, 2)
+        p = rng.uniform(0.7, 1.5)
+        out.append((int(ks[i]), density_wave_2d(int(nxs[i]), int(nys[i]), m1, m2, ph, a, u, v, p)))
+    return out
+
+
 # shock problems of Examples 4.4 and 4.5 (no positivity limiter needed)
 
 SHU_OSHER_LEFT = (3.857143, 2.629369, 10.333333)

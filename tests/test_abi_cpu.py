@@ -65,7 +65,30 @@ def test_injected_allocation_failure_reports_nomem(L, monkeypatch):
     assert not h.value
 
 
+def test_batch2d_create_rejects_bad_arguments(L):
+    """Argument checks of fam_batch2d_create run before any device call."""
+    ci = ctypes.c_int * 2
+    nx, ny, k = ci(16, 20), ci(12, 8), ci(5, 4)
+    h = ctypes.c_void_p()
+    L.fam_batch2d_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_void_p]
+    args = lambda **kw: [ctypes.byref(h), kw.get("n", 2), kw.get("nx", nx), kw.get("ny", ny), kw.get("k", k),
+                         0.0, 1.0, 0.0, kw.get("y1", 1.0), kw.get("eq", 2), kw.get("bc", 0), 1.4,
+                         kw.get("prec", 64), None]
+    assert L.fam_batch2d_create(*args(ny=None)) == 1
+    assert L.fam_batch2d_create(*args(n=0)) == 1
+    assert L.fam_batch2d_create(*args(k=ci(5, 7))) == 1
+    assert L.fam_batch2d_create(*args(ny=ci(12, 3))) == 1
+    assert L.fam_batch2d_create(*args(y1=0.0)) == 1
+    assert L.fam_batch2d_create(*args(bc=2)) == 1
+    assert L.fam_batch2d_create(*args(eq=0)) == 7  # FAM_E_UNSUPPORTED: the 2D batch is for 2D Euler
+    assert not h.value
+
+
 def test_null_handle_calls_are_rejected(L):
+    assert L.fam_batch_tile(None, None, None) == 1
     assert L.fam_step(None, 0.3) == 1
     assert L.fam_sync(None) == 1
     assert L.fam_set_option(None, b"oe_type", 2.0) == 1

@@ -100,3 +100,88 @@ def test_batch_reports_nonphysical_state():
     with pytest.raises(fam.FamError) as e:
         b.sync()
     assert e.value.code == 4
+
+
+# ----------------------------------------------------------------------------
+# 2D batches (2D Euler)
+# ----------------------------------------------------------------------------
+
+def _instances_2d(seed=0):
+    rng = np.random.default_rng(seed)
+    shapes = [(40, 24, 3), (33, 17, 4), (64, 40, 5), (20, 36, 6), (48, 48, 5), (70, 45, 4), (17, 9, 6)]
+    states = []
+    for nx, ny, _ in shapes:
+        ph = rng.uniform(0, 2 * np.pi, 4)
+        amp = rng.uniform(0.05, 0.15)
+        f = lambda X, Y, ph=ph, amp=amp: inputs.primitive_to_conservative_2d(
+            1 + amp * np.sin(2 * np.pi * (X + Y) + ph[0]), 0.3 + amp * np.cos(2 * np.pi * X + ph[1]),
+            -0.2 + amp * np.sin(2 * np.pi * Y + ph[2]), 1 + amp * np.cos(2 * np.pi * (X - Y) + ph[3]))
+        states.append(inputs.project_2d(f, nx, ny))
+    return [s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], states
+
+
+@pytest.mark.parametrize("bc", [fam.PERIODIC, fam.OUTFLOW])
+def test_batch2d_matches_single_problem_bitwise_and_oracle(bc):
+    nx, ny, ks, states = _instances_2d(3)
+    b = fam.Batch(nx, ks, ny=ny, bc=bc)
+    b.set_state(states)
+    b.run(20, 0.4)
+    b.sync()
+    got = b.get_state()
+    t, dt, steps = b.times()
+    assert np.all(steps == 20)
+    assert len(set(np.round(dt, 15))) > 1  # instances take their own step sizes
+    info = b.info()
+    tile = fam.TILES_2D.index((info["tile_x"], info["tile_y"]))
+    obc = oracle.OUTFLOW if bc == fam.OUTFLOW else oracle.PERIODIC
+    for i, (n, m, k, U) in enumerate(zip(nx, ny, ks, states)):
+        with fam.Solver(2, n, m, k=k, equation=fam.EULER, bc=bc, tile2d=tile) as s:
+            s.set_state(U)
+            s.run_steps(20, 0.4)
+            single = s.get_state()
+            ts, _, _ = s.time()
+        assert np.array_equal(got[i], single), i
+        assert ts == t[i]
+        if i % 2 == 0:
+            P = oracle.Problem(d=2, nx=n, ny=m, k=k, eq=oracle.EULER, bc=(obc,) * 4)
+            want, tw, _ = oracle.run(P, U, nsteps=20, cfl=0.4)
+            assert _comp_err(got[i], want) < 1e-12, (i, _comp_err(got[i], want))
+            assert abs(tw - t[i]) < 1e-13
+        if bc == fam.PERIODIC:
+            for c in range(4):
+                assert abs(got[i][c, 0].sum() - U[c, 0].sum()) < 1e-12 * abs(U[c, 0].sum())
+
+
+def test_batch2d_tuner_and_tile_shapes():
+    nx, ny, ks, states = _instances_2d(5)
+    P = [oracle.Problem(d=2, nx=n, ny=m, k=k, eq=oracle.EULER) for n, m, k in zip(nx, ny, ks)]
+    want = [oracle.run(p, U, nsteps=8, cfl=0.4)[0] for p, U in zip(P, states)]
+    b = fam.Batch(nx, ks, ny=ny, bc=fam.PERIODIC)
+    for tile in (0, 1, 2):
+        b.set_option("tile2d", tile)
+        b.set_state(states)
+        b.run(8, 0.4)
+        b.sync()
+        for g, w in zip(b.get_state(), want):
+            assert _comp_err(g, w) < 1e-12
+    b.set_state(states)
+    tx, bps = b.tune(0.4, probe_steps=2)
+    info = b.info()
+    assert tx == info["tile_x"] and (info["tile_x"], info["tile_y"]) in fam.TILES_2D and bps >= 1
+    b.set_state(states)
+    b.run(8, 0.4)
+    b.sync()
+    for g, w in zip(b.get_state(), want):
+        assert _comp_err(g, w) < 1e-12
+
+
+def test_batch2d_reports_nonphysical_state():
+    nx, ny, ks, states = _instances_2d(6)
+    states[1] = states[1].copy()
+    states[1][0, 0, 5, 5] = -1.0
+    b = fam.Batch(nx, ks, ny=ny)
+    b.set_state(states)
+    b.run(2, 0.4)
+    with pytest.raises(fam.FamError) as e:
+        b.sync()
+    assert e.value.code == 4

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2609_26194_b300 import fam, inputs
-from test_gpu_parity import assert_parity, comp_err, smooth_state
+from test_gpu_parity import assert_parity, comp_err, rounding_spread, smooth_state
 
 pytestmark = pytest.mark.gpu
 
@@ -55,21 +55,6 @@ def test_reflective_and_mixed_2d(bcs):
     assert_parity(s.get_state(), want)
 
 
-def _rounding_spread(P, U, cfl, T=None, nsteps=None, seeds=(1, 2)):
-    """Largest component-relative change of the oracle's own result when its
-    input is perturbed by 2e-16 relative noise (the rounding sensitivity of
-    the run)."""
-    base, _, _ = oracle.run(P, U, T=T, nsteps=nsteps, cfl=cfl)
-    B = base.reshape(base.shape[0], -1)
-    out = 0.0
-    for seed in seeds:
-        Up = U * (1.0 + 2e-16 * np.random.default_rng(seed).standard_normal(U.shape))
-        b, _, _ = oracle.run(P, Up, T=T, nsteps=nsteps, cfl=cfl)
-        d = np.max(np.abs(b.reshape(B.shape) - B), axis=1) / np.max(np.abs(B), axis=1)
-        out = max(out, float(d.max()))
-    return base, out
-
-
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
 def test_shu_osher_inflow_outflow(k):
     """Example 4.4: 400 cells on [-5,5], left boundary the pre-shock state,
@@ -103,7 +88,7 @@ def test_shu_osher_inflow_outflow(k):
     t, _, _ = s.time()
     assert t == 1.8
     got = s.get_state()
-    want, spread = _rounding_spread(P, U, cfl, T=1.8)
+    want, spread = rounding_spread(P, U, cfl, T=1.8)
     assert 0.0 < spread < 0.1
     assert comp_err(got, want) < 10.0 * spread, (comp_err(got, want), spread)
     rho = got[0, 0]
