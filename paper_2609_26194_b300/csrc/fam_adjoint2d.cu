@@ -32,74 +32,11 @@ namespace {
 using fam::cidx;
 
 // ------------------------------------------------------------------------
-// evaluation points: the 16 volume points (row b = eta node, column a = xi
-// node), the 4 faces' Gauss points, in a fixed per-cell order:
-//   slots 0..15  volume (b*4 + a)
+// point slots of a cell, in a fixed order:
+//   slots 0..15  volume (b*4 + a): xi node a, eta node b (ascending nodes)
 //   slots 16..19 x-face -1/2 (eta node g), 20..23 x-face +1/2,
 //   slots 24..27 y-face -1/2 (xi node g), 28..31 y-face +1/2
 // ------------------------------------------------------------------------
-template <typename T, int K>
-__device__ __forceinline__ void eval_points(const T* c, T* v) {
-  constexpr int D = K - 1;
-  const double* X = famgen::kGaussX;
-  // P_a at the Gauss nodes and at +-1/2 through the symmetric rows
-  auto P = [&](int a, double x) -> T {
-    const double ax = fabs(x);
-    double val;
-    if (ax == 0.5) val = famgen::kLegAt[kRowHalf][a];
-    else if (ax < 0.3) val = famgen::kLegAt[kRowInner][a];
-    else val = famgen::kLegAt[kRowOuter][a];
-    if ((a & 1) && x < 0) val = -val;
-    return T(val);
-  };
-#pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    double xi, eta;
-    if (q < 16) { xi = X[q % 4]; eta = X[q / 4]; }
-    else if (q < 20) { xi = -0.5; eta = X[q - 16]; }
-    else if (q < 24) { xi = 0.5; eta = X[q - 20]; }
-    else if (q < 28) { xi = X[q - 24]; eta = -0.5; }
-    else { xi = X[q - 28]; eta = 0.5; }
-    T s = T(0);
-#pragma unroll
-    for (int d = 0; d <= D; ++d)
-#pragma unroll
-      for (int a = 0; a <= d; ++a) s = fma(c[cidx(a, d - a)], P(a, xi) * P(d - a, eta), s);
-    v[q] = s;
-  }
-}
-
-// transpose of eval_points: cb[l] = sum_q B[q][l] vb[q]
-template <typename T, int K>
-__device__ __forceinline__ void eval_points_T(const T* vb, T* cb) {
-  constexpr int D = K - 1;
-  constexpr int NCO = K * (K + 1) / 2;
-  const double* X = famgen::kGaussX;
-  auto P = [&](int a, double x) -> T {
-    const double ax = fabs(x);
-    double val;
-    if (ax == 0.5) val = famgen::kLegAt[kRowHalf][a];
-    else if (ax < 0.3) val = famgen::kLegAt[kRowInner][a];
-    else val = famgen::kLegAt[kRowOuter][a];
-    if ((a & 1) && x < 0) val = -val;
-    return T(val);
-  };
-#pragma unroll
-  for (int l = 0; l < NCO; ++l) cb[l] = T(0);
-#pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    double xi, eta;
-    if (q < 16) { xi = X[q % 4]; eta = X[q / 4]; }
-    else if (q < 20) { xi = -0.5; eta = X[q - 16]; }
-    else if (q < 24) { xi = 0.5; eta = X[q - 20]; }
-    else if (q < 28) { xi = X[q - 24]; eta = -0.5; }
-    else { xi = X[q - 28]; eta = 0.5; }
-#pragma unroll
-    for (int d = 0; d <= D; ++d)
-#pragma unroll
-      for (int a = 0; a <= d; ++a) cb[cidx(a, d - a)] = fma(P(a, xi) * P(d - a, eta), vb[q], cb[cidx(a, d - a)]);
-  }
-}
 
 template <int K> struct RT;
 #define FAM_RT(K, FCT)                                                                         \
@@ -140,26 +77,45 @@ __device__ __forceinline__ void gather_patch_g(const T* __restrict__ U, const Ge
 template <typename T, int K, class PH>
 __global__ void __launch_bounds__(128) adj_traces(const T* __restrict__ U, const Geo geo, T* __restrict__ TR) {
   constexpr int NC = PH::NC;
+  constexpr int D = K - 1;
+  constexpr int NCO = K * (K + 1) / 2;
   const long long n = (long long)geo.nx * geo.ny;
   const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (cell >= n) return;
   const int i = (int)(cell % geo.nx), j = (int)(cell / geo.nx);
+  auto put = [&](int f, int g, int c, T v) { TR[((long long)(f * 4 + g) * NC + c) * n + cell] = v; };
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    T A[9], X[9], Y[9], t[4];
+    T A[9], X[9], Y[9], coef[NCO];
     gather_patch_g(U, geo, c, j, i, A, X, Y);
-    Recon2D<K>::tr_xm(A, X, Y, t);
+    Recon2D<K>::coef(A, X, Y, coef);
+    // x-faces at the eta nodes: pairs (+inner, -inner) = nodes (2, 1), (+outer, -outer) = (3, 0)
 #pragma unroll
-    for (int g = 0; g < 4; ++g) TR[((0 * 4 + g) * NC + c) * n + cell] = t[g];
-    Recon2D<K>::tr_xp(A, X, Y, t);
+    for (int pr = 0; pr < 2; ++pr) {
+      T dp[D + 1], dm[D + 1];
+      if (pr == 0) eta_pair<T, D, kRowInner>(coef, dp, dm);
+      else eta_pair<T, D, kRowOuter>(coef, dp, dm);
+      const int hp = pr == 0 ? 2 : 3, hm = pr == 0 ? 1 : 0;
+      T rp, lp, rm, lm;
+      sym_pair<T, D, kRowHalf>(dp, rp, lp);
+      sym_pair<T, D, kRowHalf>(dm, rm, lm);
+      put(1, hp, c, rp);
+      put(0, hp, c, lp);
+      put(1, hm, c, rm);
+      put(0, hm, c, lm);
+    }
+    // y-faces at the xi nodes: eta = +1/2 (top, face 3) and -1/2 (bottom, face 2)
+    T dp[D + 1], dm[D + 1], t[4], b[4];
+    eta_pair<T, D, kRowHalf>(coef, dp, dm);
+    sym_pair<T, D, kRowInner>(dp, t[2], t[1]);
+    sym_pair<T, D, kRowOuter>(dp, t[3], t[0]);
+    sym_pair<T, D, kRowInner>(dm, b[2], b[1]);
+    sym_pair<T, D, kRowOuter>(dm, b[3], b[0]);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) TR[((1 * 4 + g) * NC + c) * n + cell] = t[g];
-    Recon2D<K>::tr_ym(A, X, Y, t);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) TR[((2 * 4 + g) * NC + c) * n + cell] = t[g];
-    Recon2D<K>::tr_yp(A, X, Y, t);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) TR[((3 * 4 + g) * NC + c) * n + cell] = t[g];
+    for (int g = 0; g < 4; ++g) {
+      put(3, g, c, t[g]);
+      put(2, g, c, b[g]);
+    }
   }
 }
 
@@ -194,63 +150,88 @@ __device__ __forceinline__ void llf_vjp(const PH& ph, int dir, const T* uL, cons
 
 // PB[(s*3 + m)*NC + comp][cell]: cotangent of this cell's patch input
 // (neighbour s of the 3x3 patch, moment m) from R^T v.
+//
+// Point cotangents (16 volume points, 16 face Gauss points; slots as
+// listed at the top of this file) go to shared memory, [q][c][thread]; each component's
+// coefficient cotangents are then the transposed sum-factorised evaluation
+// (sym_pair_T / eta_pair_T mirror the forward evaluation of stage2d).
+constexpr int kAdjBS = 64;  // threads per block of adj_residual_local
+
 template <typename T, int K, class PH>
-__global__ void __launch_bounds__(128) adj_residual_local(const T* __restrict__ U, const Geo geo,
-                                                          const T* __restrict__ TR, const T* __restrict__ V,
-                                                          const PH ph, T* __restrict__ PB) {
+__global__ void __launch_bounds__(kAdjBS) adj_residual_local(const T* __restrict__ U, const Geo geo,
+                                                             const T* __restrict__ TR, const T* __restrict__ V,
+                                                             const PH ph, T* __restrict__ PB) {
   constexpr int NC = PH::NC;
+  constexpr int D = K - 1;
   constexpr int NCO = K * (K + 1) / 2;
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  T* vbs = reinterpret_cast<T*>(adj_smem);  // [32][NC][kAdjBS]
+  auto VB = [&](int q, int c) -> T& { return vbs[(q * NC + c) * kAdjBS + threadIdx.x]; };
   const long long n = (long long)geo.nx * geo.ny;
   const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (cell >= n) return;
+  if (cell >= n) return;  // no block-wide barrier below
   const int i = (int)(cell % geo.nx), j = (int)(cell / geo.nx);
   const T idx_ = T(geo.idx), idy_ = T(geo.idy);
   const double* X = famgen::kGaussX;
   const double* W = famgen::kGaussW;
-  // cotangent v of R at this cell and its four neighbours: V[(c*3 + m)][cell]
   auto vat = [&](int c, int m, int jj, int ii) -> T {
     return V[(long long)(c * 3 + m) * n + (long long)wrap(jj, geo.ny) * geo.nx + wrap(ii, geo.nx)];
   };
   auto trat = [&](int f, int g, int c, int jj, int ii) -> T {
     return TR[(long long)((f * 4 + g) * NC + c) * n + (long long)wrap(jj, geo.ny) * geo.nx + wrap(ii, geo.nx)];
   };
-  // point cotangents per component: vb[c][32]
-  T vb[NC][32];
-  T coef[NC][NCO];
-  T pv[NC][32];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    T A[9], Xm[9], Ym[9];
-    gather_patch_g(U, geo, c, j, i, A, Xm, Ym);
-    Recon2D<K>::coef(A, Xm, Ym, coef[c]);
-    eval_points<T, K>(coef[c], pv[c]);
-#pragma unroll
-    for (int q = 0; q < 32; ++q) vb[c][q] = T(0);
-  }
-  // volume points: V1 = sum W f1 -> R1 = V1/dx ; V2 -> R2 = V2/dy
-  T v1[NC], v2[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    v1[c] = vat(c, 1, j, i) * idx_;
-    v2[c] = vat(c, 2, j, i) * idy_;
-  }
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    T u[NC], ub[NC], w1[NC], w2[NC];
-    const T wq = T(W[q % 4] * W[q / 4]);
+  // ---- volume points: flux Jacobian-transposes weighted by v1/dx, v2/dy ----
+  {
+    T coef[NC][NCO];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      u[c] = pv[c][q];
-      ub[c] = T(0);
-      w1[c] = wq * v1[c];
-      w2[c] = wq * v2[c];
+      T A[9], Xm[9], Ym[9];
+      gather_patch_g(U, geo, c, j, i, A, Xm, Ym);
+      Recon2D<K>::coef(A, Xm, Ym, coef[c]);
     }
-    ph.flux_vjp(0, u, w1, ub);
-    ph.flux_vjp(1, u, w2, ub);
+    T v1[NC], v2[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) vb[c][q] += ub[c];
+    for (int c = 0; c < NC; ++c) {
+      v1[c] = vat(c, 1, j, i) * idx_;
+      v2[c] = vat(c, 2, j, i) * idy_;
+    }
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+      T up[NC][4], um[NC][4];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T dp[D + 1], dm[D + 1];
+        if (pr == 0) eta_pair<T, D, kRowInner>(coef[c], dp, dm);
+        else eta_pair<T, D, kRowOuter>(coef[c], dp, dm);
+        sym_pair<T, D, kRowInner>(dp, up[c][2], up[c][1]);
+        sym_pair<T, D, kRowOuter>(dp, up[c][3], up[c][0]);
+        sym_pair<T, D, kRowInner>(dm, um[c][2], um[c][1]);
+        sym_pair<T, D, kRowOuter>(dm, um[c][3], um[c][0]);
+      }
+      const int hp = pr == 0 ? 2 : 3, hm = pr == 0 ? 1 : 0;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int b = side == 0 ? hp : hm;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T wq = T(W[a] * W[b]);
+          T u[NC], ub[NC], w1[NC], w2[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            u[c] = side == 0 ? up[c][a] : um[c][a];
+            ub[c] = T(0);
+            w1[c] = wq * v1[c];
+            w2[c] = wq * v2[c];
+          }
+          ph.flux_vjp(0, u, w1, ub);
+          ph.flux_vjp(1, u, w2, ub);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) VB(b * 4 + a, c) = ub[c];
+        }
+      }
+    }
   }
-  // faces.  x-face between L and R at Gauss node g (eta):
+  // ---- faces.  x-face between L and R at Gauss node g (eta):
   //   Fbar = (w_g/dx)[-v0_L - v1_L/2 - eta_g v2_L + v0_R - v1_R/2 + eta_g v2_R]
   // y-face between B and T at xi node g:
   //   Fbar = (w_g/dy)[-v0_B - v2_B/2 - xi_g v1_B + v0_T - v2_T/2 + xi_g v1_T]
@@ -286,19 +267,49 @@ __global__ void __launch_bounds__(128) adj_residual_local(const T* __restrict__ 
       if (side == 0) llf_vjp(ph, dir, own, oth, Fb, 0, ub);
       else llf_vjp(ph, dir, oth, own, Fb, 1, ub);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) vb[c][16 + f * 4 + g] += ub[c];
+      for (int c = 0; c < NC; ++c) VB(16 + f * 4 + g, c) = ub[c];
     }
   }
-  // transpose of evaluation and of the reconstruction
-#pragma unroll
+  // ---- transpose of the point evaluation, then of the reconstruction ----
+#pragma unroll 1
   for (int c = 0; c < NC; ++c) {
-    T cb[NCO], gp[27];
-    eval_points_T<T, K>(vb[c], cb);
+    T cb[NCO];
+#pragma unroll
+    for (int l = 0; l < NCO; ++l) cb[l] = T(0);
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+      const int hp = pr == 0 ? 2 : 3, hm = pr == 0 ? 1 : 0;
+      T dpb[D + 1], dmb[D + 1];
+#pragma unroll
+      for (int a = 0; a <= D; ++a) dpb[a] = dmb[a] = T(0);
+      // volume values at eta = +node (row hp) and -node (row hm)
+      sym_pair_T<T, D, kRowInner>(VB(hp * 4 + 2, c), VB(hp * 4 + 1, c), dpb);
+      sym_pair_T<T, D, kRowOuter>(VB(hp * 4 + 3, c), VB(hp * 4 + 0, c), dpb);
+      sym_pair_T<T, D, kRowInner>(VB(hm * 4 + 2, c), VB(hm * 4 + 1, c), dmb);
+      sym_pair_T<T, D, kRowOuter>(VB(hm * 4 + 3, c), VB(hm * 4 + 0, c), dmb);
+      // x-face traces (xi = +1/2: slot 20 + node, -1/2: slot 16 + node) on the same eta rows
+      sym_pair_T<T, D, kRowHalf>(VB(20 + hp, c), VB(16 + hp, c), dpb);
+      sym_pair_T<T, D, kRowHalf>(VB(20 + hm, c), VB(16 + hm, c), dmb);
+      if (pr == 0) eta_pair_T<T, D, kRowInner>(dpb, dmb, cb);
+      else eta_pair_T<T, D, kRowOuter>(dpb, dmb, cb);
+    }
+    {
+      // y-face traces: eta = +1/2 (slots 28 + xi node), -1/2 (slots 24 + xi node)
+      T dpb[D + 1], dmb[D + 1];
+#pragma unroll
+      for (int a = 0; a <= D; ++a) dpb[a] = dmb[a] = T(0);
+      sym_pair_T<T, D, kRowInner>(VB(28 + 2, c), VB(28 + 1, c), dpb);
+      sym_pair_T<T, D, kRowOuter>(VB(28 + 3, c), VB(28 + 0, c), dpb);
+      sym_pair_T<T, D, kRowInner>(VB(24 + 2, c), VB(24 + 1, c), dmb);
+      sym_pair_T<T, D, kRowOuter>(VB(24 + 3, c), VB(24 + 0, c), dmb);
+      eta_pair_T<T, D, kRowHalf>(dpb, dmb, cb);
+    }
+    T gp[27];
     RT<K>::coefT(cb, gp);
 #pragma unroll
-    for (int s = 0; s < 9; ++s)
+    for (int s2 = 0; s2 < 9; ++s2)
 #pragma unroll
-      for (int m = 0; m < 3; ++m) PB[(long long)((s * 3 + m) * NC + c) * n + cell] = gp[m * 9 + s];
+      for (int m = 0; m < 3; ++m) PB[(long long)((s2 * 3 + m) * NC + c) * n + cell] = gp[m * 9 + s2];
   }
 }
 
@@ -584,6 +595,13 @@ static cudaError_t adj_step(fam_handle* h, AdjBuffers& B, const void* const* S /
   const int grid = (int)((n + bs - 1) / bs);
   const double gk = h->gamma_k > 0.0 ? h->gamma_k : (K <= 4 ? 25.0 : 15.0);
   const double* U3 = reinterpret_cast<const double*>(S[3]);
+  const size_t adj_res_smem = sizeof(double) * 32 * PH::NC * kAdjBS;  // 64 KB: above the default 48 KB
+  {
+    // per call (cheap), so that it holds on whichever device is current
+    cudaError_t ea = cudaFuncSetAttribute(adj_residual_local<double, K, PH>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_res_smem);
+    if (ea != cudaSuccess) return ea;
+  }
   // OE transpose: lam (post-OE) -> tmp (pre-OE)
   adj_oe_prep<double, K, PH><<<grid, bs, 0, h->stream>>>(U3, geo, ph, h->oe_q6, B.TRC, B.SP);
   adj_oe_local<double, K, PH><<<grid, bs, 0, h->stream>>>(U3, geo, ph, B.TRC, B.SP, B.lam, dt, gk, B.JB, B.AVB,
@@ -603,7 +621,8 @@ static cudaError_t adj_step(fam_handle* h, AdjBuffers& B, const void* const* S /
   for (int s = 3; s >= 1; --s) {
     const double* Us = reinterpret_cast<const double*>(S[s - 1]);
     adj_traces<double, K, PH><<<grid, bs, 0, h->stream>>>(Us, geo, B.TR);
-    adj_residual_local<double, K, PH><<<grid, bs, 0, h->stream>>>(Us, geo, B.TR, B.tmp, ph, B.PB);
+    adj_residual_local<double, K, PH><<<(int)((n + kAdjBS - 1) / kAdjBS), kAdjBS, adj_res_smem, h->stream>>>(
+        Us, geo, B.TR, B.tmp, ph, B.PB);
     // out_in goes to lam (reused as the next v); acc collects U^n cotangents
     adj_gather<double, 4><<<grid, bs, 0, h->stream>>>(B.PB, B.tmp, geo, dt, w0s[s], w1s[s], s, B.lam, B.acc);
     e = cudaGetLastError();

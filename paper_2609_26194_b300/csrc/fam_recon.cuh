@@ -67,6 +67,28 @@ __device__ __forceinline__ void eta_pair(const T* c, T* dp, T* dm) {
   }
 }
 
+// Transposes (for the adjoint): given the cotangents vpb, vmb of the pair
+// (vp, vm) of sym_pair, accumulate the cotangents of d; given dpb, dmb of
+// eta_pair's outputs, accumulate the cotangents of the coefficients c.
+template <typename T, int D, int ROW>
+__device__ __forceinline__ void sym_pair_T(T vpb, T vmb, T* db) {
+  const T e = vpb + vmb, o = vpb - vmb;
+  db[0] += e;
+#pragma unroll
+  for (int a = 1; a <= D; ++a) db[a] = fma(T(famgen::kLegAt[ROW][a]), (a & 1) ? o : e, db[a]);
+}
+
+template <typename T, int D, int ROW>
+__device__ __forceinline__ void eta_pair_T(const T* dpb, const T* dmb, T* cb) {
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    const T e = dpb[a] + dmb[a], o = dpb[a] - dmb[a];
+    cb[cidx(a, 0)] += e;
+#pragma unroll
+    for (int b = 1; a + b <= D; ++b) cb[cidx(a, b)] = fma(T(famgen::kLegAt[ROW][b]), (b & 1) ? o : e, cb[cidx(a, b)]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // dispatch to the generated operators
 // ---------------------------------------------------------------------------
