@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=500)
     ap.add_argument("--batched2d-steps", type=int, default=50)
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-n", type=int, default=1024)
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint-vs-plain report and print it as one JSON line")
     return ap.parse_args()
 
 
@@ -350,10 +353,12 @@ def adjoint_report(a, torch):
     """Gradient of dx dy sum(rho) over a 64x64 window after 200 steps (1024^2,
     FAM5, FP64, checkpoints every 20) against the plain forward run."""
     from paper_2609_26194_b300 import fam, inputs
-    n, nsteps, cfl = 1024, a.adjoint_steps, 0.55
+    n, nsteps, cfl = a.adjoint_n, a.adjoint_steps, 0.55
+    ck = min(20, max(1, nsteps // 2))
     U0 = inputs.euler2d_fourier(n, seed=5)
     G = np.zeros_like(U0)
-    G[0, 0, 480:544, 480:544] = 1.0 / (n * n)
+    w0 = n // 2 - 32
+    G[0, 0, w0:w0 + 64, w0:w0 + 64] = 1.0 / (n * n)
     s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC)
     s.set_state(U0)
     s.run_steps(2, cfl)
@@ -366,15 +371,15 @@ def adjoint_report(a, torch):
     fwd_s = time.perf_counter() - t0
     torch.cuda.reset_peak_memory_stats()
     t0 = time.perf_counter()
-    grad = s.adjoint(U0, G, nsteps, cfl, ckpt_every=20)
+    grad = s.adjoint(U0, G, nsteps, cfl, ckpt_every=ck)
     adj_s = time.perf_counter() - t0
     s.close()
     state_gb = U0.nbytes / 1e9
-    return {"workload": "2D Euler FAM5 periodic 1024x1024, 200 steps, CFL 0.55, J = dx dy sum rho over "
-                        "cells [480,544)^2, checkpoints every 20", "forward_seconds": fwd_s,
+    return {"workload": f"2D Euler FAM5 periodic {n}x{n}, {nsteps} steps, CFL 0.55, J = dx dy sum rho over "
+                        f"cells [{w0},{w0 + 64})^2, checkpoints every {ck}", "forward_seconds": fwd_s,
             "forward_plus_reverse_seconds": adj_s, "ratio_vs_plain_forward": adj_s / fwd_s,
             "forward_value": 3.0 * n * n * nsteps / fwd_s, "unit": UNIT,
-            "device_memory_gb_estimate": round(state_gb * (1.05 * (nsteps // 20 + 4 * 20 + 3) + 12), 2),
+            "device_memory_gb_estimate": round(state_gb * (1.05 * (nsteps // ck + 4 * ck + 3) + 12), 2),
             "grad_norm_inf": float(np.max(np.abs(grad)))}
 
 
@@ -514,6 +519,10 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.adjoint_only:
+        import torch
+        print(json.dumps({"adjoint": adjoint_report(a, torch)}), flush=True)
+        return 0
     return run_fam(a)
 
 

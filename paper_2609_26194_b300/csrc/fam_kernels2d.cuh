@@ -384,8 +384,16 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
 
 
 // stage = 1, 2, 3: Shu--Osher stage; stage = 0: write the residual R only.
+// Resident CTAs per SM the register allocation is bounded for: FP64 needs
+// all 255 registers for the 4 x 15 coefficients of a cell (one CTA of 256 or
+// two of 128 threads fit); FP32 needs half as many, so 512 threads fit.
+template <typename T, int NT>
+constexpr int stage_min_blocks() {
+  return sizeof(T) == 8 ? 1 : (512 / NT);
+}
+
 template <typename T, int K, class PH, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 1)
+__global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
     stage2d(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_u0,
             T* __restrict__ Uout, const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
   constexpr int NC = PH::NC;
