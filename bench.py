@@ -39,16 +39,16 @@ UNIT = "cell-stage/s"
 
 # Algorithmic FP64 work per cell and stage of the stage kernel: the executed
 # DFMA / DADD / DMUL instructions of one launch per cell (ncu, 2048^2 FAM5,
-# 16x8 tiles; profiles/stage2d_k5_f64_2048.md): 1105.6 DFMA + 445.2 DADD
-# + 437.0 DMUL = 3093.4 FLOP with a DFMA counted as 2, minus the 240 FLOP per
+# 16x8 tiles; profiles/stage2d_k5_f64_2048.md): 1102.5 DFMA + 445.2 DADD
+# + 437.0 DMUL = 3087.2 FLOP with a DFMA counted as 2, minus the 240 FLOP per
 # cell that the ring cells around each 16x8 tile spend recomputing face
 # traces (48 ring cells x 4 components x 160 FLOP / 128 cells).  The count
 # excludes the ring, so it does not depend on the tile shape.
-FLOP_PER_CELL_STAGE = {(5, 64): 2853.4}
+FLOP_PER_CELL_STAGE = {(5, 64): 2847.2}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
-# dram__bytes_write.sum from the same capture, 1.1885 GB / 4.19 M cells);
+# dram__bytes_write.sum from the same capture, 1.1844 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
-DRAM_BYTES_PER_CELL = {(5, 64): 283.4}
+DRAM_BYTES_PER_CELL = {(5, 64): 282.4}
 
 
 def parse():
@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--batched2d-steps", type=int, default=50)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-n", type=int, default=1024)
+    ap.add_argument("--oracle-rate-only", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint-vs-plain report and print it as one JSON line")
     return ap.parse_args()
@@ -174,6 +175,20 @@ def oracle_rate(a, target_s: float, steps: int | None = None, sample_n: int = 25
             "kind": "oracle",
             "sample": f"{n} oracle time steps (3 stages + OE) on a {sample_n}x{sample_n} periodic sub-grid of the "
                       f"{full_n}x{full_n} FAM{a.k} workload, {el:.1f} s"}, times
+
+
+def oracle_single_thread(a, seconds: float):
+    """The same oracle sample on one host thread (a child process started
+    with OMP_NUM_THREADS=1, since OpenMP fixes its thread count at load)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-rate-only", str(seconds), "--n", str(a.n),
+           "--k", str(a.k)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, check=True).stdout
+        r = json.loads(out.strip().splitlines()[-1])
+        return {"value": r["value"], "unit": r["unit"], "cores": r["cores"], "sample": r["sample"]}
+    except (subprocess.SubprocessError, ValueError, KeyError, IndexError) as e:
+        return {"value": None, "error": str(e)[:200]}
 
 
 def run_reference(a):
@@ -506,6 +521,7 @@ def run_fam(a):
         line["adjoint"] = adjoint_report(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb, _ = oracle_rate(a, 15.0)
+        cb["single_thread"] = oracle_single_thread(a, 6.0)
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -517,6 +533,10 @@ def run_fam(a):
 
 def main():
     a = parse()
+    if a.oracle_rate_only is not None:  # child of oracle_single_thread (runs no GPU code)
+        r, _ = oracle_rate(a, a.oracle_rate_only)
+        print(json.dumps(r), flush=True)
+        return 0
     if a.impl == "reference":
         return run_reference(a)
     if a.adjoint_only:

@@ -50,7 +50,9 @@ typedef enum {
 } fam_status;
 
 typedef enum { FAM_ADVECTION = 0, FAM_BURGERS = 1, FAM_EULER = 2 } fam_equation;
-typedef enum { FAM_BC_PERIODIC = 0, FAM_BC_OUTFLOW = 1 } fam_bc;
+/* Side conditions (Remark in Sec. 2.3).  fam_create takes PERIODIC or
+ * OUTFLOW for every side; fam_set_bc sets any of the four per side. */
+typedef enum { FAM_BC_PERIODIC = 0, FAM_BC_OUTFLOW = 1, FAM_BC_REFLECTIVE = 2, FAM_BC_INFLOW = 3 } fam_bc;
 
 typedef struct {
   int d;           /* dimension: 1 or 2 */
