@@ -44,7 +44,10 @@ UNIT = "cell-stage/s"
 # cell that the ring cells around each 16x8 tile spend recomputing face
 # traces (48 ring cells x 4 components x 160 FLOP / 128 cells).  The count
 # excludes the ring, so it does not depend on the tile shape.
-FLOP_PER_CELL_STAGE = {(5, 64): 2847.2}
+# The FP32 kernel is the same code instantiated in float: the same count
+# (its reciprocals and roots are single hardware operations in FP32, a few
+# FLOP fewer per cell).
+FLOP_PER_CELL_STAGE = {(5, 64): 2847.2, (5, 32): 2847.2}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
 # dram__bytes_write.sum from the same capture, 1.1844 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
@@ -67,6 +70,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-plain report")
+    ap.add_argument("--no-configs", action="store_true", help="skip the throughput of the other workloads")
     ap.add_argument("--batched-steps", type=int, default=500)
     ap.add_argument("--batched2d-steps", type=int, default=50)
     ap.add_argument("--adjoint-steps", type=int, default=200)
@@ -364,6 +368,81 @@ def batched2d_report(a, torch):
             "status": status}
 
 
+def configs_report(a, torch):
+    """Throughput of the other workloads (seeded synthetic grids shaped like
+    the paper's tests), each timed on the device over a whole run."""
+    from paper_2609_26194_b300 import fam, inputs
+
+    def timed(solver, stream, run):
+        # events on the solver's own stream bracket its launches
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        solver.sync()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        run()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sec = s0.elapsed_time(s1) * 1e-3
+        solver.sync()  # raises on a non-physical state: the run's number would not stand
+        return sec
+
+    out = {}
+    # advection sine, N = 200, k = 3, CFL 0.2 to T = 1 (1000 steps; launch-bound by size)
+    U = inputs.advection_sine(200)
+    for prec in (64, 32):
+        st = torch.cuda.Stream()
+        s = fam.Solver(1, 200, k=3, equation=fam.ADVECTION, bc=fam.PERIODIC, gamma=1.0, precision=prec,
+                       stream=st.cuda_stream)
+        s.set_state(U.astype(np.float64 if prec == 64 else np.float32))
+        s.run_steps(1000, 0.2)  # builds the graph of 1000 steps
+        s.set_state(U.astype(np.float64 if prec == 64 else np.float32))
+        sec = timed(s, st, lambda: s.run_steps(1000, 0.2))
+        out[f"advection_N200_k3_f{prec}"] = {"value": 3.0 * 200 * 1000 / sec, "seconds": sec, "steps": 1000}
+        s.close()
+    # 1D Euler Riemann, N = 65536, k = 5, outflow, CFL 0.3, 1000 steps (one graph launch)
+    U = inputs.euler1d_riemann(65536, seed=2)
+    for prec in (64, 32):
+        st = torch.cuda.Stream()
+        s = fam.Solver(1, 65536, k=5, equation=fam.EULER, bc=fam.OUTFLOW, precision=prec, stream=st.cuda_stream)
+        s.set_state(U.astype(np.float64 if prec == 64 else np.float32))
+        s.run_steps(1000, 0.3)
+        s.set_state(U.astype(np.float64 if prec == 64 else np.float32))
+        sec = timed(s, st, lambda: s.run_steps(1000, 0.3))
+        out[f"euler1d_riemann_N65536_k5_f{prec}"] = {"value": 3.0 * 65536 * 1000 / sec, "seconds": sec,
+                                                     "steps": 1000}
+        s.close()
+    # 2D Euler 4096^2 periodic, k = 4 and 6: smooth wave and rectangles, 5 steps each (tuned tile)
+    n, steps = 4096, 5
+    data = {"smooth": inputs.euler2d_smooth(n),
+            "rectangles": inputs.euler2d_rectangles(n, seed=3, nrect=64, **inputs.ADMISSIBLE_RECT)}
+    for k in (4, 6):
+        cfl = 0.4 if k == 4 else 0.55
+        for prec in (64, 32):
+            st = torch.cuda.Stream()
+            s = fam.Solver(2, n, n, k=k, equation=fam.EULER, bc=fam.PERIODIC, precision=prec,
+                           stream=st.cuda_stream)
+            s.set_state(data["smooth"].astype(np.float64 if prec == 64 else np.float32))
+            tile = fam.TILES_2D[s.tune(cfl, probe_steps=1)]
+            for name, U in data.items():
+                s.set_state(U.astype(np.float64 if prec == 64 else np.float32))
+                s.run_steps(steps, cfl)
+                s.set_state(U.astype(np.float64 if prec == 64 else np.float32))
+                sec = timed(s, st, lambda: s.run_steps(steps, cfl))
+                out[f"euler2d_{name}_4096_k{k}_f{prec}"] = {"value": 3.0 * n * n * steps / sec, "seconds": sec,
+                                                            "steps": steps, "tile": list(tile)}
+            s.close()
+    return {"unit": UNIT, "note": "each run: CUDA events around one graph-captured multi-step launch "
+                                  "(after an untimed run of the same length)", "runs": out}
+
+
+def configs_report_safe(a, torch):
+    from paper_2609_26194_b300 import fam
+    try:
+        return configs_report(a, torch)
+    except fam.FamError as e:
+        return {"status": str(e)}
+
+
 def adjoint_report(a, torch):
     """Gradient of dx dy sum(rho) over a 64x64 window after 200 steps (1024^2,
     FAM5, FP64, checkpoints every 20) against the plain forward run."""
@@ -519,6 +598,8 @@ def run_fam(a):
         line["batched2d"] = batched2d_report(a, torch)
     if rank == 0 and world == 1 and not a.no_adjoint:
         line["adjoint"] = adjoint_report(a, torch)
+    if rank == 0 and world == 1 and not a.no_configs:
+        line["configs"] = configs_report_safe(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb, _ = oracle_rate(a, 15.0)
         cb["single_thread"] = oracle_single_thread(a, 6.0)
