@@ -463,3 +463,26 @@ def test_tile_autotuner_keeps_parity(tmp_path):
     s2, _ = make(2, n, 5, "euler", "periodic")
     s2.set_state(U)
     assert s2.tune(0.5, probe_steps=2, cache_path=cache) == choice  # cached
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_smallest_grids(bc):
+    """The smallest grids the library takes (4 cells per direction): one tile
+    covers the grid several times over and the ring and ghost cells wrap onto
+    interior cells."""
+    for k in (3, 6):
+        s, P = make(1, 4, k, "euler", bc)
+        U = smooth_state(1, 4, seed=40)
+        s.set_state(U)
+        s.run_steps(10, 0.3)
+        s.sync()
+        want, _, _ = oracle.run(P, U, nsteps=10, cfl=0.3)
+        assert_parity(s.get_state(), want)
+        for n in ((4, 4), (5, 4), (4, 9)):
+            s, P = make(2, n, k, "euler", bc)
+            U = smooth_state(2, n, seed=41)
+            s.set_state(U)
+            s.run_steps(10, 0.4)
+            s.sync()
+            want, _, _ = oracle.run(P, U, nsteps=10, cfl=0.4)
+            assert_parity(s.get_state(), want)
