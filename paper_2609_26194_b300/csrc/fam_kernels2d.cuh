@@ -175,6 +175,13 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   constexpr int D = K - 1;
   constexpr int NCOEF = Recon2D<K>::NCOEF;
   constexpr int NT = TX * TY;
+  // Face slots, face index fastest ([Gauss point][component][face]), so that
+  // neighbouring threads touch neighbouring words (no shared-memory bank
+  // conflicts): x-faces (row, col) with col 0..TX, y-faces (row, col) with
+  // row 0..TY.
+  constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+  auto XI = [](int row, int col, int g, int c) { return (g * NC + c) * NFX + row * (TX + 1) + col; };
+  auto YI = [](int row, int col, int g, int c) { return (g * NC + c) * NFY + row * TX + col; };
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int hx = tx + 2, hy = ty + 2;
@@ -211,10 +218,10 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
       sym_pair<T, D, kRowHalf>(dp, rp, lp);
       sym_pair<T, D, kRowHalf>(dm, rm, lm);
       // this cell's right trace = left side of x-face tx+1; left trace = right side of face tx
-      xL[((ty * (TX + 1) + tx + 1) * 4 + hp) * NC + c] = rp;
-      xL[((ty * (TX + 1) + tx + 1) * 4 + hm) * NC + c] = rm;
-      xR[((ty * (TX + 1) + tx) * 4 + hp) * NC + c] = lp;
-      xR[((ty * (TX + 1) + tx) * 4 + hm) * NC + c] = lm;
+      xL[XI(ty, tx + 1, hp, c)] = rp;
+      xL[XI(ty, tx + 1, hm, c)] = rm;
+      xR[XI(ty, tx, hp, c)] = lp;
+      xR[XI(ty, tx, hm, c)] = lm;
     }
     const int hp = pr == 0 ? 2 : 3, hm = pr == 0 ? 1 : 0;
 #pragma unroll
@@ -240,8 +247,8 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     sym_pair<T, D, kRowOuter>(dm, b[3], b[0]);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-      yB[(((ty + 1) * TX + tx) * 4 + g) * NC + c] = t[g];
-      yT[((ty * TX + tx) * 4 + g) * NC + c] = b[g];
+      yB[YI(ty + 1, tx, g, c)] = t[g];
+      yT[YI(ty, tx, g, c)] = b[g];
     }
   }
   // Ring cells around the tile: only the trace facing the tile, one task per
@@ -258,21 +265,21 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     constexpr int NR = 2 * (TX + TY);
     for (int task = threadIdx.x; task < NR * NC; task += NT) {
       const int r = task % NR, c = task / NR;
-      int rx, ry, ox, oy, swap;
+      int rx, ry, ox, oy, swap, fstride;
       unsigned long long xsign;
       T* out;
       if (r < TY) {  // left column: its right trace = left side of x-face 0
-        rx = -1; ry = r; ox = 1; oy = HX; swap = 0; xsign = 0ull;
-        out = xL + (ry * (TX + 1) + 0) * 4 * NC;
+        rx = -1; ry = r; ox = 1; oy = HX; swap = 0; xsign = 0ull; fstride = NFX;
+        out = xL + XI(ry, 0, 0, 0);
       } else if (r < 2 * TY) {  // right column: its left trace = right side of x-face TX
-        rx = TX; ry = r - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull;
-        out = xR + (ry * (TX + 1) + TX) * 4 * NC;
+        rx = TX; ry = r - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; fstride = NFX;
+        out = xR + XI(ry, TX, 0, 0);
       } else if (r < 2 * TY + TX) {  // bottom row: its top trace = bottom side of y-face 0
-        rx = r - 2 * TY; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull;
-        out = yB + (0 * TX + rx) * 4 * NC;
+        rx = r - 2 * TY; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; fstride = NFY;
+        out = yB + YI(0, rx, 0, 0);
       } else {  // top row: its bottom trace = top side of y-face TY
-        rx = r - 2 * TY - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull;
-        out = yT + (TY * TX + rx) * 4 * NC;
+        rx = r - 2 * TY - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; fstride = NFY;
+        out = yT + YI(TY, rx, 0, 0);
       }
       const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + (ry + 2) * HX + (rx + 2);
       const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * HY * HX + (ry + 2) * HX + (rx + 2);
@@ -287,30 +294,36 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
       }
       Recon2D<K>::tr_xp(A, X, Y, t);
 #pragma unroll
-      for (int g = 0; g < 4; ++g) out[g * NC + c] = t[g];
+      for (int g = 0; g < 4; ++g) out[(g * NC + c) * fstride] = t[g];
     }
   }
   __syncthreads();
 
   // ---- phase B: Rusanov fluxes at every face Gauss point -----------------
-  constexpr int NXP = (TX + 1) * TY * 4, NYP = TX * (TY + 1) * 4;
+  // face point it: x-faces first (it = g * NFX + face), then y-faces
+  constexpr int NXP = NFX * 4, NYP = NFY * 4;
   for (int it = threadIdx.x; it < NXP + NYP; it += NT) {
     T uL[NC], uR[NC], fL[NC], fR[NC];
     T* slot;
     const T* other;
+    int cs;  // component stride
     T sL, sR;
     if (it < NXP) {
-      slot = xL + it * NC;
-      other = xR + it * NC;
+      const int g = it / NFX, f = it - g * NFX;
+      slot = xL + g * NC * NFX + f;
+      other = xR + g * NC * NFX + f;
+      cs = NFX;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { uL[c] = slot[c]; uR[c] = other[c]; }
+      for (int c = 0; c < NC; ++c) { uL[c] = slot[c * NFX]; uR[c] = other[c * NFX]; }
       sL = ph.flux_x(uL, fL);
       sR = ph.flux_x(uR, fR);
     } else {
-      slot = yB + (it - NXP) * NC;
-      other = yT + (it - NXP) * NC;
+      const int q = it - NXP, g = q / NFY, f = q - g * NFY;
+      slot = yB + g * NC * NFY + f;
+      other = yT + g * NC * NFY + f;
+      cs = NFY;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { uL[c] = slot[c]; uR[c] = other[c]; }
+      for (int c = 0; c < NC; ++c) { uL[c] = slot[c * NFY]; uR[c] = other[c * NFY]; }
       sL = ph.flux_y(uL, fL);
       sR = ph.flux_y(uR, fR);
     }
@@ -318,7 +331,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     // is folded into the quadrature weights of phase C (exact: a power of 2)
     const T a = max_nonneg(sL, sR);  // a NaN speed (non-physical trace) propagates
 #pragma unroll
-    for (int c = 0; c < NC; ++c) slot[c] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
+    for (int c = 0; c < NC; ++c) slot[c * cs] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
   }
   __syncthreads();
 
@@ -343,14 +356,14 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const T* fl = xL + ((ty * (TX + 1) + tx) * 4) * NC + c;
-    const T* fr = xL + ((ty * (TX + 1) + tx + 1) * 4) * NC + c;
-    const T* fb = yB + ((ty * TX + tx) * 4) * NC + c;
-    const T* ft = yB + (((ty + 1) * TX + tx) * 4) * NC + c;
+    const T* fl = xL + XI(ty, tx, 0, c);
+    const T* fr = xL + XI(ty, tx + 1, 0, c);
+    const T* fb = yB + YI(ty, tx, 0, c);
+    const T* ft = yB + YI(ty + 1, tx, 0, c);
     T sxl = T(0), sxr = T(0), syb = T(0), syt = T(0), mx = T(0), my = T(0);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-      const T a = fl[g * NC], b = fr[g * NC], cb = fb[g * NC], ct = ft[g * NC];
+      const T a = fl[g * NC * NFX], b = fr[g * NC * NFX], cb = fb[g * NC * NFY], ct = ft[g * NC * NFY];
       sxl = fma(hw[g], a, sxl);
       sxr = fma(hw[g], b, sxr);
       syb = fma(hw[g], cb, syb);
@@ -453,6 +466,9 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
   constexpr int HX = S::HX, HY = S::HY;
   constexpr int NT = TX * TY;
   constexpr int RX = TX + 2, RY = TY + 2;  // tile plus one ring
+  // face-centre trace f (0 x-, 1 x+, 2 y-, 3 y+) of component c at ring
+  // position q, position fastest (no shared-memory bank conflicts)
+  auto FI = [](int f, int c, int q) { return (f * NC + c) * (RX * RY) + q; };
 
   // Face-centre traces (Tab. sigma2d jumps need the two traces at each face
   // centre): all four of every tile cell, one task per (cell, component);
@@ -468,7 +484,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
     gather_patch<T, HX, HY>(tile, c, cx + 2, cy + 2, A, X, Y);
     Recon2D<K>::facec(A, X, Y, t, q6);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) fc[(q * 4 + f) * NC + c] = t[f];
+    for (int f = 0; f < 4; ++f) fc[FI(f, c, q)] = t[f];
   }
   for (int task = threadIdx.x; task < NR * NC; task += NT) {
     const int r = task % NR, c = task / NR;
@@ -497,7 +513,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
     }
     Recon2D<K>::facec(A, X, Y, t, q6);  // only t[1] (x = +1/2) is used
     const int q = (ry + 1) * RX + (rx + 1);
-    fc[(q * 4 + slot) * NC + c] = t[1];
+    fc[FI(slot, c, q)] = t[1];
   }
   for (int q = threadIdx.x; q < RX * RY; q += NT) {
     const int hx = q % RX + 1, hy = q / RX + 1;
@@ -524,10 +540,10 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       // jumps [[u]] = u(right/top side) - u(left/bottom side) at the four face centres
-      const T jxl = fc[(q * 4 + 0) * NC + c] - fc[((q - 1) * 4 + 1) * NC + c];
-      const T jxr = fc[((q + 1) * 4 + 0) * NC + c] - fc[(q * 4 + 1) * NC + c];
-      const T jyb = fc[(q * 4 + 2) * NC + c] - fc[((q - RX) * 4 + 3) * NC + c];
-      const T jyt = fc[((q + RX) * 4 + 2) * NC + c] - fc[(q * 4 + 3) * NC + c];
+      const T jxl = fc[FI(0, c, q)] - fc[FI(1, c, q - 1)];
+      const T jxr = fc[FI(0, c, q + 1)] - fc[FI(1, c, q)];
+      const T jyb = fc[FI(2, c, q)] - fc[FI(3, c, q - RX)];
+      const T jyt = fc[FI(2, c, q + RX)] - fc[FI(3, c, q)];
       // Type II over the 3x3 stencil: S = sum of the averages (unnormalised,
       // as printed), D = max |u_s - S| = max(S - min u, max u - S) (rounding
       // is monotone, so this equals the max of the nine rounded differences)
@@ -594,7 +610,7 @@ __global__ void __launch_bounds__(TX * TY, 1)
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
-  T* fc = tile + S::TILE;            // face-centre traces [RY][RX][4][NC]
+  T* fc = tile + S::TILE;            // face-centre traces [4][NC][RY * RX]
   T* sp = fc + 4 * NC * RX * RY;     // speeds at averages [2][RY][RX]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sp + 2 * RX * RY);
   double* red = reinterpret_cast<double*>(bar + 2);
