@@ -294,18 +294,31 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// Block-wide maximum of values >= 0 (speeds, |u|, deviations), on their bit
+// patterns with integer operations (the FP64 pipe stays free, which matters
+// most to the FP32 kernels).  A NaN or negative input counts as 0, as fmax
+// over such data would drop a NaN.
 template <int NT>
 __device__ __forceinline__ double block_max(double v, double* scratch /* >= NT/32 */) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  long long b = __double_as_longlong(v);
+  if (!(b > 0 && b <= 0x7FF0000000000000ll)) b = 0;  // NaN, negative, -0 -> +0 (+inf kept)
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long c = __shfl_xor_sync(0xffffffffu, b, o);
+    b = c > b ? c : b;
+  }
+  long long* sc = reinterpret_cast<long long*>(scratch);
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   __syncthreads();
-  if (l == 0) scratch[w] = v;
+  if (l == 0) sc[w] = b;
   __syncthreads();
   if (w == 0) {
-    v = (l < NT / 32) ? scratch[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    b = (l < NT / 32) ? sc[l] : 0ll;
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long c = __shfl_xor_sync(0xffffffffu, b, o);
+      b = c > b ? c : b;
+    }
   }
-  return v;  // valid in thread 0
+  return __longlong_as_double(b);  // valid in thread 0
 }
 
 // Called by thread 0 of every block after its atomic max.  The last block to
