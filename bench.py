@@ -37,19 +37,22 @@ sys.path.insert(0, ROOT)
 METRIC = "2D Euler k=5 cell-stage updates/s"
 UNIT = "cell-stage/s"
 
-# Algorithmic FP64 work per cell and stage of the stage kernel: the executed
-# DFMA / DADD / DMUL instructions of one launch per cell (ncu, 2048^2 FAM5,
-# 16x8 tiles; profiles/stage2d_k5_f64_2048.md): 1102.5 DFMA + 445.2 DADD
-# + 437.0 DMUL = 3087.2 FLOP with a DFMA counted as 2, minus the 240 FLOP per
-# cell that the ring cells around each 16x8 tile spend recomputing face
-# traces (48 ring cells x 4 components x 160 FLOP / 128 cells).  The count
-# excludes the ring, so it does not depend on the tile shape.
+# Algorithmic FP64 work per cell and stage of the stage kernel: the
+# DFMA / DADD / DMUL instructions of one launch per cell, counted by ncu
+# (2048^2 FAM5, 16x8 tiles; profiles/stage2d_k5_f64_2048.md) when every
+# multiply still ran on the FP64 unit: 1102.5 DFMA + 445.2 DADD + 437.0 DMUL
+# = 3087.2 FLOP with a DFMA counted as 2, minus the 240 FLOP per cell that
+# the ring cells around each 16x8 tile spend recomputing face traces (48
+# ring cells x 4 components x 160 FLOP / 128 cells).  The count excludes the
+# ring, so it does not depend on the tile shape.  The products the kernel
+# now computes on the integer pipes (bit-identical) are still FLOP of the
+# method and stay in the count.
 # The FP32 kernel is the same code instantiated in float: the same count
 # (its reciprocals and roots are single hardware operations in FP32, a few
 # FLOP fewer per cell).
 FLOP_PER_CELL_STAGE = {(5, 64): 2847.2, (5, 32): 2847.2}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
-# dram__bytes_write.sum from the same capture, 1.1844 GB / 4.19 M cells);
+# dram__bytes_write.sum of the current kernel, 1.1845 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
 DRAM_BYTES_PER_CELL = {(5, 64): 282.4}
 

@@ -285,11 +285,20 @@ fam_status fam_step1d_noalloc(const void* U_in, void* U_out, int nx, double x0, 
 fam_status fam_alu_peak(int precision, double* flops_per_s);
 
 /* Diagnostics: the library's FP64 reciprocal, reciprocal square root and
- * square root (FP32 hardware approximation refined by two Newton-Raphson
- * steps) applied to n host values x (positive, within the FP32 normal
+ * square root (FP32 hardware approximation refined by one third-order
+ * step) applied to n host values x (positive, within the FP32 normal
  * range); results are written to the three host arrays.  Test hook for
  * comparing against correctly rounded results. */
 fam_status fam_selftest_math(const double* x, int n, double* rcp, double* rsqrt, double* sqrt_out);
+
+/* Diagnostics: the library's binary64 multiply computed with integer
+ * instructions (the FP64 kernels run part of their products on the integer
+ * pipes, beside the FP64 unit), applied elementwise to the n host pairs
+ * (a[i], b[i]); prod[i] = a[i] * b[i] is written to a host array.  The IEEE
+ * 754 round-to-nearest-even product is expected bit for bit, for every
+ * input including zeros, subnormals, infinities and NaNs.  FAM_E_INVAL for
+ * null pointers or n <= 0, FAM_E_NOMEM / FAM_E_CUDA on device errors. */
+fam_status fam_selftest_int_fp64(const double* a, const double* b, int n, double* prod);
 
 #ifdef __cplusplus
 }

@@ -2,9 +2,10 @@
 //
 // Contents: the device control block (time, step size, wave-speed reduction,
 // status flags), padded-layout geometry, FP64 reciprocal / reciprocal square
-// root by Newton-Raphson refinement of the FP32 hardware approximations,
-// TMA + mbarrier wrappers (inline PTX) with bounded waits, and the
-// grid-wide max reduction with a last-block epilogue.
+// root by refinement of the FP32 hardware approximations, the binary64
+// multiply on the integer pipes, integer max / sign helpers, TMA + mbarrier
+// wrappers (inline PTX) with bounded waits, and the grid-wide max reduction
+// with a last-block epilogue.
 #pragma once
 
 #include <cuda.h>
@@ -140,6 +141,53 @@ __device__ __forceinline__ float flip_sign(float v, unsigned long long m) {
   return __uint_as_float(__float_as_uint(v) ^ (unsigned)(m >> 32));
 }
 
+// ---------------------------------------------------------------------------
+// binary64 multiply on the integer pipes
+// ---------------------------------------------------------------------------
+// On this GPU the FP64 unit retires about one warp instruction per 16 SM
+// cycles, while the integer pipes sit idle in the FP64 kernels.  dmul_int
+// computes the IEEE 754 binary64 product, rounded to nearest with ties to
+// even, with 32/64-bit integer instructions only.  The kernels use it for
+// products that no multiply-add absorbs and that sit among independent work
+// (the volume points and the reconstruction), where it runs beside the FP64
+// unit.  Its results equal the FP64 unit's bit for bit: the significand
+// product is formed exactly, then rounded on the bits below the 53rd, with a
+// sticky bit for the rest.  Zero, subnormal, infinite or NaN operands, and
+// products outside the normal range, go to the FP64 unit (__dmul_rn), which
+// keeps every special case exact.  (An add built the same way was measured
+// slower than the FP64 unit's in these kernels and is not used.)
+
+// a * b.  With the significands left-aligned in 64 bits (ma, mb in
+// [2^63, 2^64)), the 128-bit product's high word holds the significand
+// product in [2^62, 2^64); its top 53 bits are the result's significand, the
+// next bit is the rounding bit, and the remaining high bits plus the low word
+// form the sticky bit.
+__device__ __forceinline__ double dmul_int(double a, double b) {
+  const unsigned long long ia = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ib = (unsigned long long)__double_as_longlong(b);
+  const int ea = (int)((ia >> 52) & 0x7FF), eb = (int)((ib >> 52) & 0x7FF);
+  const int e = ea + eb - 1023;  // biased exponent for a significand product in [1, 2)
+  if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || (unsigned)(e - 1) >= 2044u)
+    return __dmul_rn(a, b);
+  const unsigned long long top_bit = 0x8000000000000000ull;
+  const unsigned long long ma = (ia << 11) | top_bit, mb = (ib << 11) | top_bit;
+  const unsigned long long hi = __umul64hi(ma, mb), lo = ma * mb;
+  const unsigned carry = (unsigned)(hi >> 63);  // significand product in [2, 4)
+  const unsigned drop = 10 + carry;               // bits below the 53-bit significand
+  unsigned long long m = hi >> drop;
+  const unsigned long long rest = hi << (64 - drop);  // dropped bits, left-aligned
+  m += (rest > top_bit || (rest == top_bit && (lo != 0 || (m & 1)))) ? 1ull : 0ull;
+  // the hidden bit of m adds one to the exponent field (and a rounding carry
+  // to 2^53 one more, with a zero fraction)
+  return __longlong_as_double((long long)(((ia ^ ib) & top_bit) |
+                                          (((unsigned long long)(e + (int)carry - 1) << 52) + m)));
+}
+
+// The kernels' choice of multiply: the integer-pipe one in FP64, the plain
+// one in FP32.
+__device__ __forceinline__ double pmul(double a, double b) { return dmul_int(a, b); }
+__device__ __forceinline__ float pmul(float a, float b) { return a * b; }
+
 // Max and |.| of values >= 0 through their bit patterns (non-negative IEEE
 // numbers order like their integer patterns; a NaN operand wins): integer
 // operations, off the FP64 pipe.
@@ -200,9 +248,9 @@ template <> struct Fast<double> {
     const unsigned hi = (unsigned)__double2hiint(x);
     double r = widen_f32(rsqrt_approx_f32(narrow_hi(hi)));
     r = seed_range_pos(hi) ? r : nan_f64();
-    const double xr = x * r;
+    const double xr = dmul_int(x, r);
     const double e = fma(-xr, r, 1.0);
-    return fma(xr * e, fma(0.375, e, 0.5), xr);
+    return fma(dmul_int(xr, e), fma(0.375, e, 0.5), xr);
   }
   static __device__ __forceinline__ double exp_(double x) { return exp(x); }
 };

@@ -1,7 +1,8 @@
 // fam_probe.cu -- measurement helpers exported through the C ABI: the FP64 /
 // FP32 fused multiply-add throughput of this GPU (the denominator of the
-// ALU roofline), and a check hook for the library's reciprocal and square
-// root (Newton-refined, fam_common.cuh) against the CUDA runtime's.
+// ALU roofline), a check hook for the library's reciprocal and square root
+// (refined FP32 seeds, fam_common.cuh), and one for its integer-pipe binary64
+// multiply (which must equal IEEE round-to-nearest bit for bit).
 #include <cuda_runtime.h>
 
 #include "../../include/fam.h"
@@ -60,6 +61,11 @@ __global__ void math_kernel(const double* x, int n, double* rcp, double* rsq, do
   }
 }
 
+__global__ void int_fp64_kernel(const double* a, const double* b, int n, double* prod) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) prod[i] = fam::dmul_int(a[i], b[i]);
+}
+
 }  // namespace
 
 extern "C" fam_status fam_alu_peak(int precision, double* flops_per_s) {
@@ -89,5 +95,20 @@ extern "C" fam_status fam_selftest_math(const double* x_host, int n, double* rcp
   cudaFree(a);
   cudaFree(b);
   cudaFree(c);
+  return e == cudaSuccess ? FAM_OK : FAM_E_CUDA;
+}
+
+extern "C" fam_status fam_selftest_int_fp64(const double* a_host, const double* b_host, int n, double* prod_host) {
+  if (!a_host || !b_host || n <= 0 || !prod_host) return FAM_E_INVAL;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, 3 * bytes) != cudaSuccess) return FAM_E_NOMEM;
+  double *a = buf, *b = buf + n, *p = buf + 2 * (size_t)n;
+  cudaMemcpy(a, a_host, bytes, cudaMemcpyHostToDevice);
+  cudaMemcpy(b, b_host, bytes, cudaMemcpyHostToDevice);
+  int_fp64_kernel<<<(n + 255) / 256, 256>>>(a, b, n, p);
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaMemcpy(prod_host, p, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
   return e == cudaSuccess ? FAM_OK : FAM_E_CUDA;
 }

@@ -5,7 +5,9 @@
 // systems of Sec. 2.4).  Polynomials are held in the tensor Legendre basis
 // P_a(xi) P_b(eta) with P_a monic orthogonal on [-1/2,1/2]; since
 // P_a(-x) = (-1)^a P_a(x), a value pair at +x and -x costs one even and one
-// odd partial sum (sum factorisation with symmetric pairs).
+// odd partial sum (sum factorisation with symmetric pairs).  The product
+// opening each odd sum runs on the integer pipes (pmul: bit-identical to the
+// FP64 unit's), beside the FP64 unit's multiply-adds.
 #pragma once
 
 #include "fam_common.cuh"
@@ -28,7 +30,7 @@ __device__ __forceinline__ void sym_pair(const T* d, T& vp, T& vm) {
   for (int a = 1; a <= D; ++a) {
     const T L = T(famgen::kLegAt[ROW][a]);
     if (a & 1)
-      o = (a == 1) ? d[a] * L : fma(d[a], L, o);
+      o = (a == 1) ? pmul(d[a], L) : fma(d[a], L, o);
     else
       e = fma(d[a], L, e);
   }
@@ -52,7 +54,7 @@ __device__ __forceinline__ void eta_pair(const T* c, T* dp, T* dm) {
     for (int b = 1; a + b <= D; ++b) {
       const T L = T(famgen::kLegAt[ROW][b]);
       if (b & 1) {
-        o = odd ? fma(c[cidx(a, b)], L, o) : c[cidx(a, b)] * L;
+        o = odd ? fma(c[cidx(a, b)], L, o) : pmul(c[cidx(a, b)], L);
         odd = true;
       } else {
         e = fma(c[cidx(a, b)], L, e);

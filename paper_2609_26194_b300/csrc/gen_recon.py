@@ -160,10 +160,12 @@ def _linear_terms(e):
     return d
 
 
-def emit_linear(name_out, exprs, symbols_map, indent="  ", prefix="t"):
+def emit_linear(name_out, exprs, symbols_map, indent="  ", prefix="t", lead_mul=None):
     """Emit linear forms in the inputs.  A greedy pass extracts shared scaled
     pairs x + r*y (one fused multiply-add each) while any pair occurs in at
-    least two forms; each form is then a chain of multiply-adds."""
+    least two forms; each form is then a chain of multiply-adds.  lead_mul
+    names a function that computes the product opening a chain (the one
+    product that no multiply-add absorbs)."""
     forms = [_linear_terms(e) for e in exprs]
     temps = []
     while True:
@@ -210,6 +212,8 @@ def emit_linear(name_out, exprs, symbols_map, indent="  ", prefix="t"):
                 op = "-"
             else:
                 term = f"{cnum(cf)}*{name(v)}"
+                if lead_mul and not out:
+                    term = f"{lead_mul}({cnum(cf)}, {name(v)})"
                 op = "+"
             if not out:
                 out = ("-" if op == "-" else "") + term
@@ -285,7 +289,9 @@ def gen():
         out.append(f"// ordered by total degree d, then a = 0..d (b = d - a): " + " ".join(f"({p},{r})" for p, r in keys))
         out.append("template <typename T>")
         out.append(f"__device__ __forceinline__ void fam2d_coef_k{k}(const T* A, const T* MX, const T* MY, T* c) {{")
-        out += emit_linear("c", [coef[key] for key in keys], smap)
+        # the FP64 kernels evaluate these next to other FP64 work: the opening
+        # product of each coefficient runs on the integer pipes (fam::pmul)
+        out += emit_linear("c", [coef[key] for key in keys], smap, lead_mul="fam::pmul")
         out.append("}")
         out.append("")
         # traces at the four Gauss points of each face (direct linear forms)

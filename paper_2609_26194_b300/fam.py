@@ -27,7 +27,7 @@ STATUS = {0: "FAM_OK", 1: "FAM_E_INVAL", 2: "FAM_E_NOMEM", 3: "FAM_E_CUDA", 4: "
 # every function declared in include/fam.h
 EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fam_step", "fam_run_steps",
            "fam_run", "fam_sync", "fam_time", "fam_profile", "fam_residual", "fam_oe", "fam_last_error",
-           "fam_status_string", "fam_destroy", "fam_alu_peak", "fam_selftest_math",
+           "fam_status_string", "fam_destroy", "fam_alu_peak", "fam_selftest_math", "fam_selftest_int_fp64",
            "fam_batch_create", "fam_batch_set_option", "fam_batch_set_state", "fam_batch_get_state",
            "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
            "fam_batch_last_error", "fam_batch_destroy", "fam_batch2d_create", "fam_batch_tile",
@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.fam_destroy.restype = None
         L.fam_alu_peak.argtypes = [i, dp]
         L.fam_selftest_math.argtypes = [dp, i, dp, dp, dp]
+        L.fam_selftest_int_fp64.argtypes = [dp, dp, i, dp]
         for name in EXPORTS:
             if name not in ("fam_last_error", "fam_status_string", "fam_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -265,6 +266,20 @@ def selftest_math(x: np.ndarray):
     if rc != 0:
         raise FamError(rc, "fam_selftest_math failed")
     return tuple(outs)
+
+
+def selftest_int_fp64(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """The library's integer-pipe binary64 product a * b, elementwise."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError("a and b differ in shape")
+    prod = np.empty_like(a)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().fam_selftest_int_fp64(a.ctypes.data_as(dp), b.ctypes.data_as(dp), a.size, prod.ctypes.data_as(dp))
+    if rc != 0:
+        raise FamError(rc, "fam_selftest_int_fp64 failed")
+    return prod
 
 
 class Batch:

@@ -129,6 +129,56 @@ def test_reciprocal_and_sqrt_within_few_ulp():
     assert np.all(np.isnan(rs)) and np.all(np.isnan(sq))
 
 
+def _fp64_operands(rng, n):
+    """Random binary64 bit patterns from several exponent classes: moderate,
+    the whole normal range, subnormal and zero, infinite and NaN, and short
+    significands (exact halfway cases); some second operands are -a or a
+    scaled by a power of 2, some products land near the overflow and
+    underflow thresholds."""
+    def draw(cls):
+        frac = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+        sign = rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63)
+        e = np.where(cls == 0, rng.integers(1023 - 40, 1023 + 41, n),
+            np.where(cls == 1, rng.integers(1, 2047, n),
+            np.where(cls == 2, 0,
+            np.where(cls == 3, 2047, rng.integers(1022, 1025, n))))).astype(np.uint64)
+        short = cls == 4
+        keep = rng.integers(0, 52, n).astype(np.uint64)
+        frac = np.where(short, frac & ~((np.uint64(1) << keep) - np.uint64(1)), frac)
+        frac = np.where((cls == 2) & (rng.random(n) < 0.2), np.uint64(0), frac)
+        frac = np.where((cls == 3) & (rng.random(n) < 0.5), np.uint64(0), frac)
+        return (sign | (e << np.uint64(52)) | frac).view(np.float64)
+
+    ca = rng.choice(5, n, p=[0.55, 0.2, 0.05, 0.05, 0.15])
+    cb = rng.choice(5, n, p=[0.55, 0.2, 0.05, 0.05, 0.15])
+    a, b = draw(ca), draw(cb)
+    m = rng.random(n)
+    b = np.where(m < 0.05, -a, b)
+    near = (m >= 0.05) & (m < 0.15)
+    b = np.where(near, a * np.ldexp(1.0, rng.integers(-3, 4, n)) * (1 - 2 * (rng.random(n) < 0.5)), b)
+    edge = (m >= 0.15) & (m < 0.2)
+    a = np.where(edge, np.ldexp(1.0 + rng.random(n), rng.integers(500, 520, n) * (1 - 2 * (rng.random(n) < 0.5))), a)
+    b = np.where(edge, np.ldexp(1.0 + rng.random(n), rng.integers(500, 520, n) * (1 - 2 * (rng.random(n) < 0.5))), b)
+    return a, b
+
+
+def test_integer_pipe_fp64_multiply_is_ieee_exact():
+    """The FP64 kernels run part of their products on the integer pipes: the
+    library's integer binary64 multiply must equal IEEE 754
+    round-to-nearest-even (the host's a * b) bit for bit, for normal,
+    subnormal, zero, infinite and NaN operands and for products at the
+    edges of the normal range."""
+    rng = np.random.default_rng(11)
+    a, b = _fp64_operands(rng, 1 << 22)
+    got = fam.selftest_int_fp64(a, b)
+    with np.errstate(all="ignore"):
+        want = a * b
+    same = got.view(np.uint64) == want.view(np.uint64)
+    both_nan = np.isnan(got) & np.isnan(want)
+    bad = ~(same | both_nan)
+    assert not bad.any(), (a[bad][:4], b[bad][:4], got[bad][:4], want[bad][:4])
+
+
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
 @pytest.mark.parametrize("eq,bc", [("euler", "periodic"), ("euler", "outflow"), ("adv", "periodic"),
                                    ("burgers", "outflow")])
