@@ -345,7 +345,8 @@ def gen():
             out.append("// t[0] = u(-1/2,0), t[1] = u(1/2,0), t[2] = u(0,-1/2), t[3] = u(0,1/2)")
             out.append("template <typename T>")
             out.append(f"__device__ __forceinline__ void fam2d_facec_k{k}{tag}(const T* A, const T* MX, const T* MY, T* t) {{")
-            out += emit_linear("t", [sp.expand(e) for e in tr], smap)
+            # (the OE kernel's face-centre traces: opening products on the integer pipes)
+            out += emit_linear("t", [sp.expand(e) for e in tr], smap, lead_mul="fam::pmul")
             out.append("}")
             out.append("")
     return "\n".join(out) + "\n"
