@@ -203,6 +203,16 @@ __device__ __forceinline__ float max_nonneg(float a, float b) {
   const int ia = __float_as_int(a), ib = __float_as_int(b);
   return __int_as_float(ia > ib ? ia : ib);
 }
+// a < b for a, b >= 0 (a NaN a compares false, as in IEEE), on bit patterns
+__device__ __forceinline__ bool less_nonneg(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool less_nonneg(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+// isfinite on the exponent field (integer compare instead of an FP64 one)
+__device__ __forceinline__ bool finite_bits(double v) {
+  return (__double_as_longlong(v) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool finite_bits(float v) { return (__float_as_int(v) & 0x7F800000) != 0x7F800000; }
 
 // Min / max of any two non-NaN values through order-preserving integer keys
 // (negative patterns have their magnitude bits flipped).

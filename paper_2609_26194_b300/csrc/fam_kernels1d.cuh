@@ -204,15 +204,17 @@ __device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __re
       T Dn, eps;
       if (oe_type == 1) {
         Dn = T(__longlong_as_double((long long)ctl->t1_dev_bits[c]));
-        eps = T(1e-14) * fmax(T(__longlong_as_double((long long)ctl->t1_maxabs_bits[c])), T(1));
+        eps = T(1e-14) * max_nonneg(T(__longlong_as_double((long long)ctl->t1_maxabs_bits[c])), T(1));
       } else {
+        // maxima of non-negative values on their bit patterns (integer pipes)
         const T S = vm + v0 + vp;
-        Dn = fmax(fmax(fabs(vm - S), fabs(v0 - S)), fabs(vp - S));
-        eps = T(1e-14) * fmax(fmax(fmax(fabs(vm), fabs(v0)), fabs(vp)), T(1));
+        Dn = max_nonneg(max_nonneg(abs_bits(vm - S), abs_bits(v0 - S)), abs_bits(vp - S));
+        eps = T(1e-14) * max_nonneg(max_nonneg(max_nonneg(abs_bits(vm), abs_bits(v0)), abs_bits(vp)), T(1));
       }
-      if (oe_type != 0 && !(Dn < eps)) sig = fmax(sig, gamma_k * (fabs(jl) + fabs(jr)) * Fast<T>::rcp(Dn));
+      if (oe_type != 0 && !less_nonneg(Dn, eps))
+        sig = max_nonneg(sig, gamma_k * (fabs(jl) + fabs(jr)) * Fast<T>::rcp(Dn));
     }
-    const T beta = fmax(fmax(sp[q - 1], sp[q]), sp[q + 1]);
+    const T beta = max_nonneg(max_nonneg(sp[q - 1], sp[q]), sp[q + 1]);
     const T theta = beta * dt * sig * T(geo.idx);
     const T delta = Fast<T>::exp_(-theta);
 #pragma unroll
@@ -220,7 +222,7 @@ __device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __re
       const T a = tile[(size_t)(c * 2) * HX + hx];
       const T m = tile[(size_t)(c * 2 + 1) * HX + hx] * delta;
       uavg[c] = a;
-      if (!isfinite(a) || !isfinite(m)) ok = false;
+      if (!finite_bits(a) || !finite_bits(m)) ok = false;
       store_with_ghosts(Uout, geo, c * 2 + 0, 0, i, a);
       store_with_ghosts(Uout, geo, c * 2 + 1, 0, i, m);
     }

@@ -178,9 +178,13 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   // Face slots, face index fastest ([Gauss point][component][face]), so that
   // neighbouring threads touch neighbouring words (no shared-memory bank
   // conflicts): x-faces (row, col) with col 0..TX, y-faces (row, col) with
-  // row 0..TY.
+  // row 0..TY.  The x-faces col < TX are stored row-major with pitch TX and
+  // the last column (col = TX) after them, so that a warp's two rows of a
+  // 16-wide tile fill 32 consecutive words.
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-  auto XI = [](int row, int col, int g, int c) { return (g * NC + c) * NFX + row * (TX + 1) + col; };
+  auto XI = [](int row, int col, int g, int c) {
+    return (g * NC + c) * NFX + (col < TX ? row * TX + col : TX * TY + row);
+  };
   auto YI = [](int row, int col, int g, int c) { return (g * NC + c) * NFY + row * TX + col; };
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -564,7 +568,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
         Dn = max_nonneg(S - vmin, vmax - S);  // one of the two is >= 0
         eps = T(1e-14) * max_nonneg(max_nonneg(abs_bits(vmin), abs_bits(vmax)), T(1));
       }
-      if (oe_type != 0 && !(Dn < eps)) {
+      if (oe_type != 0 && !less_nonneg(Dn, eps)) {
         const T g = gamma_k * Fast<T>::rcp(Dn);
         sig_x = max_nonneg(sig_x, g * (fabs(jxl) + fabs(jxr)));
         sig_y = max_nonneg(sig_y, g * (fabs(jyb) + fabs(jyt)));
@@ -586,7 +590,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
       uavg[c] = a;
       const T m1 = tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx] * delta;
       const T m2 = tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx] * delta;
-      if (!isfinite(a) || !isfinite(m1) || !isfinite(m2)) ok = false;
+      if (!finite_bits(a) || !finite_bits(m1) || !finite_bits(m2)) ok = false;
       store_with_ghosts(Uout, geo, c * 3 + 0, j, i, a);
       store_with_ghosts(Uout, geo, c * 3 + 1, j, i, m1);
       store_with_ghosts(Uout, geo, c * 3 + 2, j, i, m2);
