@@ -52,9 +52,9 @@ UNIT = "cell-stage/s"
 # FLOP fewer per cell).
 FLOP_PER_CELL_STAGE = {(5, 64): 2847.2, (5, 32): 2847.2}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
-# dram__bytes_write.sum of the current kernel, 1.1851 GB / 4.19 M cells);
+# dram__bytes_write.sum of the current kernel, 1.1833 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
-DRAM_BYTES_PER_CELL = {(5, 64): 282.5}
+DRAM_BYTES_PER_CELL = {(5, 64): 282.1}
 
 
 def parse():

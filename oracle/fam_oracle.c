@@ -236,14 +236,17 @@ static double phys_speed(const or_problem* P, int dir, const double* u) {
 }
 
 /* Rusanov / local Lax-Friedrichs flux; the wave speed is the larger spectral
- * radius of the two one-sided traces (reading of "Rusanov flux"). */
+ * radius of the two one-sided traces (reading of "Rusanov flux").  A trace
+ * with rho <= 0 or p <= 0 (possible without the paper's positivity limiter,
+ * while the averages stay admissible) has no spectral radius (NaN): the
+ * larger radius is then the other trace's, as IEEE maxNum (C fmax) gives. */
 static void llf(const or_problem* P, int dir, const double* uL, const double* uR, double* fh) {
   int nc = or_ncomp(P);
   double fL[4], fR[4];
   phys_flux(P, dir, uL, fL);
   phys_flux(P, dir, uR, fR);
   double aL = phys_speed(P, dir, uL), aR = phys_speed(P, dir, uR);
-  double a = aL > aR ? aL : aR;
+  double a = fmax(aL, aR);
   for (int c = 0; c < nc; ++c) fh[c] = 0.5 * (fL[c] + fR[c]) - 0.5 * a * (uR[c] - uL[c]);
 }
 

@@ -111,7 +111,7 @@ class Euler2D:
     def llf(self, uL, uR, dirn):
         fL, sL = self.flux(uL, dirn)
         fR, sR = self.flux(uR, dirn)
-        a = torch.maximum(sL, sR)
+        a = torch.fmax(sL, sR)  # a NaN radius (non-physical trace) is ignored, as C fmax does
         return 0.5 * (fL + fR) - 0.5 * a * (uR - uL)
 
     # ---- eq. (11) -------------------------------------------------------------

@@ -203,6 +203,25 @@ __device__ __forceinline__ float max_nonneg(float a, float b) {
   const int ia = __float_as_int(a), ib = __float_as_int(b);
   return __int_as_float(ia > ib ? ia : ib);
 }
+// The Rusanov speed of a face: the larger of the two one-sided spectral
+// radii (>= 0), where a NaN radius (a trace with rho <= 0 or p <= 0) is
+// ignored in favour of the other one, as IEEE maxNum (C fmax) does.  On the
+// bit patterns: adding 2^52 - 1 moves the non-negative numbers (up to +inf)
+// to [2^52 - 1, 2^63 - 1] and the NaNs past 2^63, where the signed
+// comparison ranks them below every number (NaNs with the sign bit set land
+// below 2^52 - 1); two NaNs give a NaN.
+// (The addition is unsigned, so the wrap-around is defined.)
+__device__ __forceinline__ double rusanov_speed(double aL, double aR) {
+  const unsigned long long k = 0x000FFFFFFFFFFFFFull;
+  const long long l = (long long)((unsigned long long)__double_as_longlong(aL) + k);
+  const long long r = (long long)((unsigned long long)__double_as_longlong(aR) + k);
+  return l > r ? aL : aR;
+}
+__device__ __forceinline__ float rusanov_speed(float aL, float aR) {
+  const unsigned k = 0x007FFFFFu;
+  const int l = (int)(__float_as_uint(aL) + k), r = (int)(__float_as_uint(aR) + k);
+  return l > r ? aL : aR;
+}
 // a < b for a, b >= 0 (a NaN a compares false, as in IEEE), on bit patterns
 __device__ __forceinline__ bool less_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);

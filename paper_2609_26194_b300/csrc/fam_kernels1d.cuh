@@ -99,7 +99,8 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
     T uL[NC], uR[NC], FL[NC], FR[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) { uL[c] = fL[f * NC + c]; uR[c] = fR[f * NC + c]; }
-    const T a = fmax(ph.flux_x(uL, FL), ph.flux_x(uR, FR));
+    const T sL = ph.flux_x(uL, FL), sR = ph.flux_x(uR, FR);
+    const T a = rusanov_speed(sL, sR);
 #pragma unroll
     for (int c = 0; c < NC; ++c) fL[f * NC + c] = T(0.5) * (FL[c] + FR[c]) - T(0.5) * a * (uR[c] - uL[c]);
   }

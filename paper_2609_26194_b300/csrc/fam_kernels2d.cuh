@@ -333,7 +333,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     }
     // twice the Rusanov flux, f^- + f^+ - alpha (u^+ - u^-); the factor 1/2
     // is folded into the quadrature weights of phase C (exact: a power of 2)
-    const T a = max_nonneg(sL, sR);  // a NaN speed (non-physical trace) propagates
+    const T a = rusanov_speed(sL, sR);
 #pragma unroll
     for (int c = 0; c < NC; ++c) slot[c * cs] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
   }
