@@ -203,6 +203,44 @@ def test_residual_2d(k, eq, bc):
     assert_parity(s.residual(U), oracle.residual(P, U))
 
 
+def _nonphysical_face_traces(U, k, gamma=1.4):
+    """Number of face Gauss-point traces with rho <= 0 or p <= 0 (periodic
+    2D Euler state), from the oracle's reconstruction."""
+    nc, _, ny, nx = U.shape
+    xg, _ = oracle.gauss4()
+    pts = [(s, float(e)) for s in (-0.5, 0.5) for e in xg] + [(float(e), s) for s in (-0.5, 0.5) for e in xg]
+    count = 0
+    for j in range(ny):
+        for i in range(nx):
+            cs = []
+            for c in range(nc):
+                patch = [U[c, :, (j + q // 3 - 1) % ny, (i + q % 3 - 1) % nx] for q in range(9)]
+                a, mx, my = (np.array([v[m] for v in patch]) for m in range(3))
+                cs.append(oracle.recon2d(k, a, mx, my))
+            for xi, eta in pts:
+                r, mu, mv, E = (oracle.eval2d(co, n, xi, eta) for co, n in cs)
+                if r <= 0 or (gamma - 1) * (E - 0.5 * (mu * mu + mv * mv) / r) <= 0:
+                    count += 1
+    return count
+
+
+def test_residual_2d_at_nonphysical_traces():
+    """Rectangles at the shock-run ranges (rho, p in [0.1, 5], |u|, |v| <= 1)
+    have admissible averages but face traces with rho <= 0 or p <= 0, whose
+    spectral radius is undefined.  The Rusanov speed there is the other
+    trace's (IEEE maxNum, kernels and oracle alike): the residuals agree, NaN
+    where both traces of a face have no radius."""
+    n, k = 32, 5
+    U = inputs.euler2d_rectangles(n, seed=3, nrect=64)
+    assert _nonphysical_face_traces(U, k) > 0
+    s, P = make(2, (n, n), k, "euler", "periodic")
+    got, want = s.residual(U), oracle.residual(P, U)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.isfinite(want).sum() > 0.9 * want.size
+    assert_parity(np.where(ok, got, 0.0), np.where(ok, want, 0.0))
+
+
 @pytest.mark.parametrize("d", [1, 2])
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
 def test_oe_operator(d, k):
