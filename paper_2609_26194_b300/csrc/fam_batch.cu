@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
           T* sp = faces + 2 * (TX + 2) * NC;
           T* Uo = out + I.off;
           const T gk = T(I.gamma_k);
-          double m;
+          T m;
           switch (I.k) {
             case 3: m = oe1d_tile<T, 3, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
             case 4: m = oe1d_tile<T, 4, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
             default: m = oe1d_tile<T, 6, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
           }
           m = block_max<TX>(m, red);
-          if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, m);
+          if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, (double)m);
         }
       }
       if (!grid_barrier(g, nb)) return;

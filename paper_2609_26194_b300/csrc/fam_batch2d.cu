@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(TX * TY, 1)
         } else {
           const T dt_idx = T(dtd * I.idx), dt_idy = T(dtd * I.idy);
           const T gk = T(I.gamma_k);
-          double mx, my;
+          T mx, my;
           switch (I.k) {
             case 3: oe2d_tile<T, 3, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &g->status, mx, my); break;
             case 4: oe2d_tile<T, 4, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &g->status, mx, my); break;
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(TX * TY, 1)
           mx = block_max<NT>(mx, red);
           my = block_max<NT>(my, red + 32);
           if (threadIdx.x == 0) {
-            atomic_max_nonneg(&ictl[td.x].alpha_bits, mx);
-            atomic_max_nonneg(&ictl[td.x].alpha_bits_y, my);
+            atomic_max_nonneg(&ictl[td.x].alpha_bits, (double)mx);
+            atomic_max_nonneg(&ictl[td.x].alpha_bits_y, (double)my);
           }
         }
       }

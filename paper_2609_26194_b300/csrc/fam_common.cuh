@@ -397,6 +397,30 @@ __device__ __forceinline__ double block_max(double v, double* scratch /* >= NT/3
   }
   return __longlong_as_double(b);  // valid in thread 0
 }
+// The same on FP32 values (the FP32 kernels' speeds), kept in FP32 so that
+// no thread converts to FP64 (a conversion occupies the slow FP64 pipe).
+template <int NT>
+__device__ __forceinline__ float block_max(float v, double* scratch /* >= NT/64 */) {
+  int b = __float_as_int(v);
+  if (!(b > 0 && b <= 0x7F800000)) b = 0;  // NaN, negative, -0 -> +0 (+inf kept)
+  for (int o = 16; o > 0; o >>= 1) {
+    const int c = __shfl_xor_sync(0xffffffffu, b, o);
+    b = c > b ? c : b;
+  }
+  int* sc = reinterpret_cast<int*>(scratch);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) sc[w] = b;
+  __syncthreads();
+  if (w == 0) {
+    b = (l < NT / 32) ? sc[l] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      const int c = __shfl_xor_sync(0xffffffffu, b, o);
+      b = c > b ? c : b;
+    }
+  }
+  return __int_as_float(b);  // valid in thread 0
+}
 
 // Called by thread 0 of every block after its atomic max.  The last block to
 // arrive computes the next step size from the completed maxima (time-step

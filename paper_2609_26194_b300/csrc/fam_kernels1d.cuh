@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TX)
 // OE on a staged tile (layout as for stage1d_tile); returns this thread's
 // cell speed (0 outside the grid) for the CFL reduction.
 template <typename T, int K, class PH, int TX>
-__device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __restrict__ Uout, const Geo& geo,
+__device__ __forceinline__ T oe1d_tile(const T* tile, T* tr, T* sp, T* __restrict__ Uout, const Geo& geo,
                                             const PH& ph, const T dt, const int oe_type, const T gamma_k,
                                             const int x0, unsigned int* status, const FamCtl* ctl = nullptr) {
   constexpr int NC = PH::NC;
@@ -190,7 +190,7 @@ __device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __re
   }
   __syncthreads();
   const int tx = threadIdx.x, i = x0 + tx;
-  double my_speed = 0.0;
+  T my_speed = T(0);
   if (i < geo.nx) {
     const int q = tx + 1, hx = tx + 2;
     T sig = T(0);
@@ -229,7 +229,7 @@ __device__ __forceinline__ double oe1d_tile(const T* tile, T* tr, T* sp, T* __re
     }
     if (!ok) atomicOr(status, kStatusNonFinite);
     else if (!ph.admissible(uavg)) atomicOr(status, kStatusNonPhysical);
-    my_speed = (double)sp[q];
+    my_speed = sp[q];
   }
   return my_speed;
 }
@@ -255,12 +255,12 @@ __global__ void __launch_bounds__(TX)
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;
-  const double my_speed =
+  const T my_speed =
       oe1d_tile<T, K, PH, TX>(tile, tr, sp, Uout, geo, ph, T(dtd), oe_type, gamma_k, x0, &ctl->status, ctl);
   if (!reduce) return;
-  const double mx = block_max<TX>(my_speed, red);
+  const T mx = block_max<TX>(my_speed, red);
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&ctl->alpha_bits[0], mx);
+    atomic_max_nonneg(&ctl->alpha_bits[0], (double)mx);
     step_epilogue(ctl, gridDim.x, true);
   }
 }

@@ -464,7 +464,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
                                           const Geo& geo, const PH& ph, const int oe_type, const T gamma_k,
                                           const int q6, const T dt_idx, const T dt_idy, const int x0,
                                           const int y0, const FamCtl* t1, unsigned int* status,
-                                          double& my_speed_x, double& my_speed_y) {
+                                          T& my_speed_x, T& my_speed_y) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int HX = S::HX, HY = S::HY;
@@ -529,13 +529,21 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
     sp[q] = sx;
     sp[RX * RY + q] = sy;
   }
+  // Type I: the grid statistics D and eps per component, converted to T once
+  // per block (no per-cell conversion on the FP64 pipe)
+  __shared__ T t1s[2 * NC];
+  if (oe_type == 1 && t1 != nullptr && threadIdx.x < NC) {
+    const int c = threadIdx.x;
+    t1s[c] = T(__longlong_as_double((long long)t1->t1_dev_bits[c]));
+    t1s[NC + c] = T(1e-14) * max_nonneg(T(__longlong_as_double((long long)t1->t1_maxabs_bits[c])), T(1));
+  }
   __syncthreads();
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i = x0 + tx, j = y0 + ty;
   const bool inside = i < geo.nx && j < geo.ny;
-  my_speed_x = 0.0;
-  my_speed_y = 0.0;
+  my_speed_x = T(0);
+  my_speed_y = T(0);
   if (inside) {
     const int rx = tx + 1, ry = ty + 1, q = ry * RX + rx;
     const int hx = tx + 2, hy = ty + 2;
@@ -562,8 +570,8 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
       }
       T Dn = T(0), eps;
       if (oe_type == 1) {
-        Dn = T(__longlong_as_double((long long)t1->t1_dev_bits[c]));
-        eps = T(1e-14) * max_nonneg(T(__longlong_as_double((long long)t1->t1_maxabs_bits[c])), T(1));
+        Dn = t1s[c];
+        eps = t1s[NC + c];
       } else {
         Dn = max_nonneg(S - vmin, vmax - S);  // one of the two is >= 0
         eps = T(1e-14) * max_nonneg(max_nonneg(abs_bits(vmin), abs_bits(vmax)), T(1));
@@ -597,8 +605,8 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
     }
     if (!ok) atomicOr(status, kStatusNonFinite);
     else if (!ph.admissible(uavg)) atomicOr(status, kStatusNonPhysical);
-    my_speed_x = (double)sp[q];
-    my_speed_y = (double)sp[RX * RY + q];
+    my_speed_x = sp[q];
+    my_speed_y = sp[RX * RY + q];
   }
 }
 
@@ -628,15 +636,15 @@ __global__ void __launch_bounds__(TX * TY, 1)
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
 
-  double my_speed_x, my_speed_y;
+  T my_speed_x, my_speed_y;
   oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, dt_idx, dt_idy, x0, y0, ctl,
                               &ctl->status, my_speed_x, my_speed_y);
   if (!reduce) return;
-  const double mx = block_max<NT>(my_speed_x, red);
-  const double my = block_max<NT>(my_speed_y, red + 32);
+  const T mx = block_max<NT>(my_speed_x, red);
+  const T my = block_max<NT>(my_speed_y, red + 32);
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&ctl->alpha_bits[0], mx);
-    atomic_max_nonneg(&ctl->alpha_bits[1], my);
+    atomic_max_nonneg(&ctl->alpha_bits[0], (double)mx);
+    atomic_max_nonneg(&ctl->alpha_bits[1], (double)my);
     step_epilogue(ctl, gridDim.x * gridDim.y, true);
   }
 }
