@@ -574,12 +574,12 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
         eps = t1s[NC + c];
       } else {
         Dn = max_nonneg(S - vmin, vmax - S);  // one of the two is >= 0
-        eps = T(1e-14) * max_nonneg(max_nonneg(abs_bits(vmin), abs_bits(vmax)), T(1));
+        eps = pmul(T(1e-14), max_nonneg(max_nonneg(abs_bits(vmin), abs_bits(vmax)), T(1)));
       }
       if (oe_type != 0 && !less_nonneg(Dn, eps)) {
-        const T g = gamma_k * Fast<T>::rcp(Dn);
-        sig_x = max_nonneg(sig_x, g * (fabs(jxl) + fabs(jxr)));
-        sig_y = max_nonneg(sig_y, g * (fabs(jyb) + fabs(jyt)));
+        const T g = pmul(gamma_k, Fast<T>::rcp(Dn));
+        sig_x = max_nonneg(sig_x, pmul(g, fabs(jxl) + fabs(jxr)));
+        sig_y = max_nonneg(sig_y, pmul(g, fabs(jyb) + fabs(jyt)));
       }
     }
     T bx = T(0), by = T(0);
@@ -589,15 +589,16 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
       bx = max_nonneg(bx, sp[qq]);
       by = max_nonneg(by, sp[RX * RY + qq]);
     }
-    const T theta = fma(bx * sig_x, dt_idx, by * sig_y * dt_idy);
+    // (products on the integer pipes: pmul, bit-identical to the FP64 unit's)
+    const T theta = fma(pmul(bx, sig_x), dt_idx, pmul(pmul(by, sig_y), dt_idy));
     const T delta = Fast<T>::exp_(-theta);
     T uavg[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const T a = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
       uavg[c] = a;
-      const T m1 = tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx] * delta;
-      const T m2 = tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx] * delta;
+      const T m1 = pmul(tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx], delta);
+      const T m2 = pmul(tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx], delta);
       if (!finite_bits(a) || !finite_bits(m1) || !finite_bits(m2)) ok = false;
       store_with_ghosts(Uout, geo, c * 3 + 0, j, i, a);
       store_with_ghosts(Uout, geo, c * 3 + 1, j, i, m1);
