@@ -157,6 +157,19 @@ fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps);
  * number of profiled steps.  Synchronises the stream. */
 fam_status fam_profile(fam_t h, double* ms, long* nsteps);
 
+/* Number of face quadrature points (1D: faces) at which one of the two
+ * traces entering the Rusanov flux had no spectral radius, summed over every
+ * residual evaluation (the three stages of each step, fam_residual) since the
+ * last fam_set_state.  A trace has none when it is not an admissible Euler
+ * state in the sense gamma p / rho < 0 (rho <= 0 or p <= 0 at a face point,
+ * which the paper's optional positivity limiter (Sec. 2.3 remarks, Alg. 1)
+ * would prevent and this library does not build); the flux then takes the
+ * other trace's radius (IEEE maxNum, Sec. 2.3 Rusanov flux).  Faces counted:
+ * x-faces 0..nx of every row and y-faces 0..ny of every column, four Gauss
+ * points each in 2D; a periodic grid counts its boundary face twice (both
+ * images are evaluated).  Synchronous.  Errors: FAM_E_INVAL (null pointer). */
+fam_status fam_nonphysical_traces(fam_t h, unsigned long long* count);
+
 /* Semi-discrete right-hand side R(U) of eq. (1dSemi) / eq. (11) for the
  * state U (layout above), written to R (same layout).  Uses the handle's
  * scratch buffers; the handle's current state is not changed. */
@@ -219,7 +232,14 @@ fam_status fam_batch2d_create(fam_batch_t* out, int n_inst, const int* nx, const
 /* Keys: "oe_type" (0 / 2), "gamma_k" (<= 0: defaults per order), "ax",
  * "tile_x" (1D: 64 / 128 / 256 cells per tile), "tile2d" (2D: 0 / 1 / 2 for
  * 32x8 / 32x4 / 16x8 cells per tile), "blocks_per_sm" (<= 0: the occupancy
- * maximum). */
+ * maximum), "wait_limit_ns" (how long a block waits at the persistent
+ * kernel's grid barrier before the launch gives up with FAM_E_TIMEOUT from
+ * fam_batch_sync; 0 restores the default of 2 s; at most 60 s),
+ * "test_barrier_extra" (test hook, 0 or 1: the grid barrier waits for one
+ * arrival more than there are blocks, so every wait runs out after
+ * "wait_limit_ns"; the kernel then exits and fam_batch_sync reports
+ * FAM_E_TIMEOUT).  After a timeout the batch's state is undefined until the
+ * next fam_batch_set_state, which also resets the barrier. */
 fam_status fam_batch_set_option(fam_batch_t h, const char* key, double value);
 /* Copy the concatenated state in / out (on_device as in fam_set_state);
  * set_state resets every instance's clock. */
@@ -234,6 +254,14 @@ fam_status fam_batch_sync(fam_batch_t h);
 /* Per-instance time, next step size and steps taken (arrays of n_inst; any
  * may be NULL).  Synchronous. */
 fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps);
+/* Per-instance health (arrays of n_inst; any may be NULL): ntrace as
+ * fam_nonphysical_traces for the instance; status FAM_OK or
+ * FAM_E_NONPHYSICAL (a non-finite value, or averages with rho <= 0 or
+ * p <= 0, after some step); bad_step the 1-based step whose output was first
+ * flagged (0: none).  A flagged instance stops after that step (its state is
+ * that step's output) while the other instances go on; fam_batch_sync then
+ * reports FAM_E_NONPHYSICAL for the batch.  Synchronous. */
+fam_status fam_batch_health(fam_batch_t h, unsigned long long* ntrace, int* status, long* bad_step);
 /* Launch shape: tile width (2D: the tile's x extent), blocks of the
  * persistent grid, tiles, cells. */
 fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, long* cells);
@@ -269,11 +297,12 @@ void fam_batch_destroy(fam_batch_t h);
  * make the first call on each device before any stream capture.  Every call
  * reuses the same array: calls whose GPU work may overlap (other streams or
  * host threads) race and must be serialised by the caller.  stream: a
- * cudaStream_t or NULL for the legacy default stream.  If dt_used is not
- * NULL the call synchronises the stream, writes the step size taken and
- * reports FAM_E_NONPHYSICAL / FAM_E_TIMEOUT from the device flags;
- * otherwise it is asynchronous.  Errors: FAM_E_INVAL (including nx above the
- * limit), FAM_E_CUDA.
+ * cudaStream_t or NULL for the legacy default stream.  Synchronous: the
+ * call waits for its stream, then reports FAM_E_NONPHYSICAL (a non-finite
+ * value or a non-physical average) or FAM_E_TIMEOUT (a bounded wait gave up)
+ * from the device flags, and writes the step size taken to *dt_used if
+ * dt_used is not NULL.  Errors: FAM_E_INVAL (including nx above the limit),
+ * FAM_E_CUDA.
  * ------------------------------------------------------------------------ */
 #define FAM_NOALLOC_MAX_CELLS 16384
 fam_status fam_step1d_noalloc(const void* U_in, void* U_out, int nx, double x0, double x1, int k, int equation,

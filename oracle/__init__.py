@@ -129,6 +129,12 @@ def lib():
         L.or_step.argtypes = [pp, dp, ctypes.c_double]
         L.or_run.argtypes = [pp, dp, ctypes.c_double, ctypes.c_long, ctypes.c_double, ctypes.c_int,
                              dp, ctypes.POINTER(ctypes.c_long)]
+        L.or_trace_count.argtypes = []
+        L.or_trace_count.restype = ctypes.c_longlong
+        L.or_trace_reset.argtypes = []
+        L.or_trace_reset.restype = None
+        L.or_inadmissible.argtypes = [pp, dp]
+        L.or_inadmissible.restype = ctypes.c_longlong
         _lib_handle = L
     return _lib_handle
 
@@ -230,3 +236,24 @@ def run(P: Problem, U, T: float | None = None, nsteps: int | None = None, cfl: f
     if rc:
         raise FloatingPointError("oracle run produced a non-finite state")
     return U, t.value, s.value
+
+
+def trace_count(reset: bool = False) -> int:
+    """Face quadrature points at which a Rusanov trace had no spectral radius
+    (an Euler trace with gamma p / rho < 0), summed over every residual
+    evaluation since the last reset (see or_trace_count in fam_oracle.h)."""
+    n = int(lib().or_trace_count())
+    if reset:
+        lib().or_trace_reset()
+    return n
+
+
+def trace_reset() -> None:
+    lib().or_trace_reset()
+
+
+def inadmissible(P: Problem, U) -> int:
+    """Cells whose averages are not admissible (Euler: rho <= 0 or p <= 0) or
+    hold a non-finite value."""
+    U = _state(P, U)
+    return int(lib().or_inadmissible(ctypes.byref(P._c()), _ptr(U)))

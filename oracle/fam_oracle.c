@@ -240,7 +240,7 @@ static double phys_speed(const or_problem* P, int dir, const double* u) {
  * with rho <= 0 or p <= 0 (possible without the paper's positivity limiter,
  * while the averages stay admissible) has no spectral radius (NaN): the
  * larger radius is then the other trace's, as IEEE maxNum (C fmax) gives. */
-static void llf(const or_problem* P, int dir, const double* uL, const double* uR, double* fh) {
+static int llf(const or_problem* P, int dir, const double* uL, const double* uR, double* fh) {
   int nc = or_ncomp(P);
   double fL[4], fR[4];
   phys_flux(P, dir, uL, fL);
@@ -248,7 +248,15 @@ static void llf(const or_problem* P, int dir, const double* uL, const double* uR
   double aL = phys_speed(P, dir, uL), aR = phys_speed(P, dir, uR);
   double a = fmax(aL, aR);
   for (int c = 0; c < nc; ++c) fh[c] = 0.5 * (fL[c] + fR[c]) - 0.5 * a * (uR[c] - uL[c]);
+  /* 1 when a trace has no spectral radius (counted by the residuals) */
+  return isnan(aL) || isnan(aR);
 }
+
+/* Face quadrature points at which a one-sided trace had no spectral radius,
+ * summed over every residual evaluation since the last or_trace_reset(). */
+static long long g_nonphys_traces = 0;
+long long or_trace_count(void) { return g_nonphys_traces; }
+void or_trace_reset(void) { g_nonphys_traces = 0; }
 
 /* ------------------------------------------------------------------ */
 /* Ghost cells (Remark in Sec. 2.3)                                     */
@@ -381,15 +389,17 @@ static int residual_1d(const or_problem* P, padded* A, double* R) {
   for (int i = -1; i <= nx; ++i)
     for (int c = 0; c < nc; ++c) cell_coeffs(P, A, c, 0, i, &C[((size_t)(i + 1) * nc + c) * 6]);
   /* face f sits between cells f-1 and f */
-#pragma omp parallel for
+  long long bad = 0;
+#pragma omp parallel for reduction(+ : bad)
   for (int f = 0; f <= nx; ++f) {
     double uL[4], uR[4];
     for (int c = 0; c < nc; ++c) {
       uL[c] = or_eval1d(ncoef, &C[((size_t)(f) * nc + c) * 6], 0.5);
       uR[c] = or_eval1d(ncoef, &C[((size_t)(f + 1) * nc + c) * 6], -0.5);
     }
-    llf(P, 0, uL, uR, &F[(size_t)f * nc]);
+    bad += llf(P, 0, uL, uR, &F[(size_t)f * nc]);
   }
+  g_nonphys_traces += bad;
 #pragma omp parallel for
   for (int i = 0; i < nx; ++i) {
     double vol[4] = {0, 0, 0, 0};
@@ -427,7 +437,8 @@ static int residual_2d(const or_problem* P, padded* A, double* R) {
   for (int j = -1; j <= ny; ++j)
     for (int i = -1; i <= nx; ++i)
       for (int c = 0; c < nc; ++c) cell_coeffs(P, A, c, j, i, CC(j, i, c));
-#pragma omp parallel for
+  long long bad = 0;
+#pragma omp parallel for reduction(+ : bad)
   for (int j = 0; j < ny; ++j)
     for (int f = 0; f <= nx; ++f)
       for (int g = 0; g < 4; ++g) {
@@ -436,9 +447,9 @@ static int residual_2d(const or_problem* P, padded* A, double* R) {
           uL[c] = or_eval2d(ncoef, CC(j, f - 1, c), 0.5, gx[g]);
           uR[c] = or_eval2d(ncoef, CC(j, f, c), -0.5, gx[g]);
         }
-        llf(P, 0, uL, uR, &Fx[(((size_t)j * (nx + 1) + f) * 4 + g) * nc]);
+        bad += llf(P, 0, uL, uR, &Fx[(((size_t)j * (nx + 1) + f) * 4 + g) * nc]);
       }
-#pragma omp parallel for
+#pragma omp parallel for reduction(+ : bad)
   for (int f = 0; f <= ny; ++f)
     for (int i = 0; i < nx; ++i)
       for (int g = 0; g < 4; ++g) {
@@ -447,8 +458,9 @@ static int residual_2d(const or_problem* P, padded* A, double* R) {
           uB[c] = or_eval2d(ncoef, CC(f - 1, i, c), gx[g], 0.5);
           uT[c] = or_eval2d(ncoef, CC(f, i, c), gx[g], -0.5);
         }
-        llf(P, 1, uB, uT, &Fy[(((size_t)f * nx + i) * 4 + g) * nc]);
+        bad += llf(P, 1, uB, uT, &Fy[(((size_t)f * nx + i) * 4 + g) * nc]);
       }
+  g_nonphys_traces += bad;
 #pragma omp parallel for
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -697,6 +709,33 @@ int or_oe(const or_problem* P, double dt, double* U, double* theta) {
 /* ------------------------------------------------------------------ */
 /* SSP-RK3 step and time loop                                           */
 /* ------------------------------------------------------------------ */
+
+static size_t state_len(const or_problem* P);
+
+/* Number of cells whose averages are not an admissible Euler state: rho <= 0
+ * or p <= 0, i.e. rho E - |rho v|^2 / 2 <= 0 (Sec. 2.3; 0 for scalar laws)
+ * or that hold a non-finite value in any plane. */
+long long or_inadmissible(const or_problem* P, const double* U) {
+  size_t cells = (size_t)P->nx * (P->d == 1 ? 1 : P->ny);
+  int nm = or_nmom(P), nc = or_ncomp(P);
+  long long bad = 0;
+  for (size_t q = 0; q < cells; ++q) {
+    int ok = 1;
+    for (int p = 0; p < nc * nm; ++p)
+      if (!isfinite(U[(size_t)p * cells + q])) ok = 0;
+    if (ok && P->eq == OR_EULER) {
+      double rho = U[q], E = U[(size_t)(nc - 1) * nm * cells + q];
+      double m2 = 0.0;
+      for (int c = 1; c < nc - 1; ++c) {
+        double m = U[(size_t)c * nm * cells + q];
+        m2 += m * m;
+      }
+      if (!(rho > 0.0) || !(rho * E - 0.5 * m2 > 0.0)) ok = 0;
+    }
+    bad += !ok;
+  }
+  return bad;
+}
 
 static size_t state_len(const or_problem* P) {
   return (size_t)or_ncomp(P) * or_nmom(P) * P->nx * (P->d == 1 ? 1 : P->ny);

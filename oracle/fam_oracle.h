@@ -63,6 +63,20 @@ void or_gauss4(double node[4], double weight[4]);
 /* Semi-discrete right-hand side R(U) of eq. (1dSemi) / eq. (11). */
 int or_residual(const or_problem* P, const double* U, double* R);
 
+/* Face quadrature points (1D: faces) at which one of the two traces of the
+ * Rusanov flux has no spectral radius -- an Euler trace with gamma p / rho < 0
+ * (rho <= 0 or p <= 0 without a positivity limiter), whose radius |v_n| + c
+ * evaluates to NaN -- summed over every residual evaluation (stages of
+ * or_step / or_run and or_residual) since the last or_trace_reset().  The
+ * faces counted are the x-faces 0..nx of every row and the y-faces 0..ny of
+ * every column (a periodic grid counts its boundary face twice). */
+long long or_trace_count(void);
+void or_trace_reset(void);
+
+/* Cells whose averages are not admissible (Euler: rho <= 0 or p <= 0) or
+ * hold a non-finite value; 0 when the state is admissible. */
+long long or_inadmissible(const or_problem* P, const double* U);
+
 /* Maximum Rusanov wave speeds over the mesh from cell averages. */
 void or_max_speed(const or_problem* P, const double* U, double* ax, double* ay);
 

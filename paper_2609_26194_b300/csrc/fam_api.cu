@@ -727,6 +727,15 @@ fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps) {
   return FAM_OK;
 }
 
+fam_status fam_nonphysical_traces(fam_t h, unsigned long long* count) {
+  if (!h || !count) return FAM_E_INVAL;
+  FamCtl c;
+  fam_status s = ctl_read(h, &c);
+  if (s) return s;
+  *count = c.ntrace;
+  return FAM_OK;
+}
+
 fam_status fam_profile(fam_t h, double* ms, long* nsteps) {
   if (!h || !ms) return FAM_E_INVAL;
   FAM_CUDA(h, cudaStreamSynchronize(h->stream));

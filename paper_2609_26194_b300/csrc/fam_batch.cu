@@ -93,7 +93,11 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
     for (int i = blockIdx.x * TX + threadIdx.x; i < ninst; i += nb * TX) {
       const double a = __longlong_as_double((long long)ictl[i].alpha_bits);
       double dt = cfl * inst[i].dx / a;
-      if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; atomicOr(&g->status, kStatusNonFinite); }
+      if (!(dt > 0.0) || !isfinite(dt)) {
+        dt = 0.0;
+        ictl[i].status |= kStatusNonFinite;
+        atomicOr(&g->status, kStatusNonFinite);
+      }
       ictl[i].dt = dt;
       ictl[i].alpha_bits = 0ull;
     }
@@ -119,11 +123,12 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
           T* fR = faces + (TX + 1) * NC;
           const T* U0 = A + I.off;
           T* Uo = out + I.off;
+          unsigned long long* nt = &ictl[td.x].ntrace;
           switch (I.k) {
-            case 3: stage1d_tile<T, 3, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
-            case 4: stage1d_tile<T, 4, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
-            case 5: stage1d_tile<T, 5, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
-            default: stage1d_tile<T, 6, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y); break;
+            case 3: stage1d_tile<T, 3, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            case 4: stage1d_tile<T, 4, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            case 5: stage1d_tile<T, 5, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            default: stage1d_tile<T, 6, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
           }
         } else {
           T* tr = faces;
@@ -132,10 +137,10 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
           const T gk = T(I.gamma_k);
           T m;
           switch (I.k) {
-            case 3: m = oe1d_tile<T, 3, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
-            case 4: m = oe1d_tile<T, 4, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
-            case 5: m = oe1d_tile<T, 5, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
-            default: m = oe1d_tile<T, 6, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &g->status); break;
+            case 3: m = oe1d_tile<T, 3, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &ictl[td.x].status); break;
+            case 4: m = oe1d_tile<T, 4, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &ictl[td.x].status); break;
+            case 5: m = oe1d_tile<T, 5, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &ictl[td.x].status); break;
+            default: m = oe1d_tile<T, 6, PH, TX>(tile, tr, sp, Uo, geo, ph, dt, oe_type, gk, td.y, &ictl[td.x].status); break;
           }
           m = block_max<TX>(m, red);
           if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, (double)m);
@@ -151,8 +156,9 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
         c.steps += 1;
         const double a = __longlong_as_double((long long)c.alpha_bits);
         double dt = cfl * inst[i].dx / a;
-        if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; atomicOr(&g->status, kStatusNonFinite); }
+        if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; c.status |= kStatusNonFinite; }
         c.dt = dt;
+        close_instance_step(c, &g->status);
       }
       c.alpha_bits = 0ull;
       ictl[i] = c;
@@ -203,6 +209,12 @@ __global__ void fill_ghosts_batch2d(T* U, const BatchInst* inst, int ninst, int 
 // 2D tile shapes, the same as the single-problem 2D kernels'
 constexpr int kBatchTile2D[3][2] = {{32, 8}, {32, 4}, {16, 8}};
 
+// Set the barrier's wait limit and test hook (leaves the barrier state alone).
+__global__ void batch_glob_limits(BatchGlobal* g, unsigned long long wait_ns, unsigned int extra) {
+  g->wait_ns = wait_ns;
+  g->extra = extra;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -227,6 +239,8 @@ struct fam_batch {
   int tile_x = 128;
   int blocks_per_sm = 0;  // 0: occupancy maximum
   int grid = 0;
+  unsigned long long wait_ns = 0;  // grid-barrier wait limit (0: kWaitLimitNs)
+  unsigned int barrier_extra = 0;  // test hook: arrivals the barrier waits for in vain
   void* buf[3] = {nullptr, nullptr, nullptr};
   BatchCtl* ictl = nullptr;
   BatchGlobal* glob = nullptr;
@@ -359,6 +373,8 @@ static fam_status fill_ghosts(fam_batch* h, int b) {
 static fam_status reset_clock(fam_batch* h) {
   FAMB_CUDA(h, cudaMemsetAsync(h->ictl, 0, sizeof(BatchCtl) * h->n, h->stream));
   FAMB_CUDA(h, cudaMemsetAsync(h->glob, 0, sizeof(BatchGlobal), h->stream));
+  batch_glob_limits<<<1, 1, 0, h->stream>>>(h->glob, h->wait_ns, h->barrier_extra);
+  FAMB_CUDA(h, cudaGetLastError());
   return FAM_OK;
 }
 
@@ -530,6 +546,20 @@ fam_status fam_batch_set_option(fam_batch_t h, const char* key, double v) {
     return build_tiles(h);
   } else if (k == "blocks_per_sm") {
     h->blocks_per_sm = (int)v;
+  } else if (k == "wait_limit_ns" || k == "test_barrier_extra") {
+    // read by the kernels from the batch's device block at run time: no
+    // re-capture, and the step sizes stay valid
+    if (k == "wait_limit_ns") {
+      if (!(v >= 0.0) || v > 6.0e10) return bfail(h, FAM_E_INVAL, "wait_limit_ns must be in [0, 6e10]");
+      h->wait_ns = (unsigned long long)v;
+    } else {
+      if (v != 0.0 && v != 1.0) return bfail(h, FAM_E_INVAL, "test_barrier_extra must be 0 or 1");
+      h->barrier_extra = (unsigned int)v;
+    }
+    batch_glob_limits<<<1, 1, 0, h->stream>>>(h->glob, h->wait_ns, h->barrier_extra);
+    FAMB_CUDA(h, cudaGetLastError());
+    FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FAM_OK;
   } else {
     return bfail(h, FAM_E_INVAL, "unknown option " + k);
   }
@@ -656,6 +686,19 @@ fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps) {
     if (t) t[i] = c[i].t;
     if (dt) dt[i] = c[i].dt;
     if (steps) steps[i] = (long)c[i].steps;
+  }
+  return FAM_OK;
+}
+
+fam_status fam_batch_health(fam_batch_t h, unsigned long long* ntrace, int* status, long* bad_step) {
+  if (!h) return FAM_E_INVAL;
+  std::vector<BatchCtl> c(h->n);
+  FAMB_CUDA(h, cudaMemcpyAsync(c.data(), h->ictl, sizeof(BatchCtl) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->n; ++i) {
+    if (ntrace) ntrace[i] = c[i].ntrace;
+    if (status) status[i] = c[i].status == 0u ? FAM_OK : FAM_E_NONPHYSICAL;
+    if (bad_step) bad_step[i] = (long)c[i].bad_step;
   }
   return FAM_OK;
 }

@@ -19,27 +19,52 @@ struct BatchInst {
 };
 
 // Per-instance clock: step size, time, speed maxima of the current step
-// (x and y, as bit patterns of non-negative doubles), steps taken.
+// (x and y, as bit patterns of non-negative doubles), steps taken; the
+// instance's own health: face points whose trace had no spectral radius,
+// status bits, and the step whose output was first flagged (0: none; the
+// instance stops after that step while the others go on).
 struct BatchCtl {
   double dt, t;
   unsigned long long alpha_bits, alpha_bits_y;
   unsigned long long steps;
+  unsigned long long ntrace;
+  unsigned int status, pad;
+  unsigned long long bad_step;
 };
 
+// End of an instance's step in the clock pass: a flagged instance records
+// the step and stops (dt = 0); its flags join the batch's status word.
+__device__ __forceinline__ void close_instance_step(BatchCtl& c, unsigned int* gstatus) {
+  if (c.status != 0u) {
+    if (c.bad_step == 0ull) c.bad_step = c.steps;
+    c.dt = 0.0;
+    atomicOr(gstatus, c.status);
+  }
+}
+
+// Barrier state and status word of a batch, plus the barrier's wait limit
+// (wait_ns, 0: kWaitLimitNs) and a test hook: `extra` arrivals that never
+// come are added to the barrier's expected count, so that a test can make
+// the bounded wait run out (nothing hangs: every waiter gives up after
+// wait_ns and the kernel returns with kStatusTimeout).
 struct BatchGlobal {
   unsigned int bar_count, bar_gen, abort, status;
+  unsigned int extra, pad;
+  unsigned long long wait_ns;
 };
 
 // Grid-wide barrier of a cooperative launch, with a bounded wait: a block
-// that waits longer than kWaitLimitNs (or sees another block give up)
-// records a timeout and returns false so that the whole kernel exits.
-__device__ inline bool grid_barrier(BatchGlobal* g, unsigned int nblocks) {
+// that waits longer than the limit (or sees another block give up) records a
+// timeout and returns false so that the whole kernel exits.
+__device__ inline bool grid_barrier(BatchGlobal* g, unsigned int nblocks_launched) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     volatile unsigned int* vgen = &g->bar_gen;
     volatile unsigned int* vab = &g->abort;
+    const unsigned int nblocks = nblocks_launched + g->extra;
+    const unsigned long long limit = g->wait_ns != 0ull ? g->wait_ns : kWaitLimitNs;
     const unsigned int my = atomicAdd(&g->bar_gen, 0u);
     __threadfence();
     if (atomicAdd(&g->bar_count, 1u) == nblocks - 1) {
@@ -50,7 +75,7 @@ __device__ inline bool grid_barrier(BatchGlobal* g, unsigned int nblocks) {
       const unsigned long long t0 = global_ns();
       while (*vgen == my) {
         if (*vab) { ok = 0; break; }
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit) {
           atomicExch(&g->abort, 1u);
           atomicOr(&g->status, kStatusTimeout);
           ok = 0;

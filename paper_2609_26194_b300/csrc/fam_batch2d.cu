@@ -99,7 +99,11 @@ __global__ void __launch_bounds__(TX * TY, 1)
       const double ax = __longlong_as_double((long long)ictl[i].alpha_bits);
       const double ay = __longlong_as_double((long long)ictl[i].alpha_bits_y);
       double dt = cfl / (ax / inst[i].dx + ay / inst[i].dy);
-      if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; atomicOr(&g->status, kStatusNonFinite); }
+      if (!(dt > 0.0) || !isfinite(dt)) {
+        dt = 0.0;
+        ictl[i].status |= kStatusNonFinite;
+        atomicOr(&g->status, kStatusNonFinite);
+      }
       ictl[i].dt = dt;
       ictl[i].alpha_bits = 0ull;
       ictl[i].alpha_bits_y = 0ull;
@@ -126,20 +130,20 @@ __global__ void __launch_bounds__(TX * TY, 1)
           const U0FromGlobal<T> u0src{A + I.off};
           const T dt = T(dtd);
           switch (I.k) {
-            case 3: stage2d_tile<T, 3, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src); break;
-            case 4: stage2d_tile<T, 4, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src); break;
-            case 5: stage2d_tile<T, 5, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src); break;
-            default: stage2d_tile<T, 6, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src); break;
+            case 3: stage2d_tile<T, 3, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
+            case 4: stage2d_tile<T, 4, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
+            case 5: stage2d_tile<T, 5, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
+            default: stage2d_tile<T, 6, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
           }
         } else {
           const T dt_idx = T(dtd * I.idx), dt_idy = T(dtd * I.idy);
           const T gk = T(I.gamma_k);
           T mx, my;
           switch (I.k) {
-            case 3: oe2d_tile<T, 3, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &g->status, mx, my); break;
-            case 4: oe2d_tile<T, 4, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &g->status, mx, my); break;
-            case 5: oe2d_tile<T, 5, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &g->status, mx, my); break;
-            default: oe2d_tile<T, 6, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &g->status, mx, my); break;
+            case 3: oe2d_tile<T, 3, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &ictl[td.x].status, mx, my); break;
+            case 4: oe2d_tile<T, 4, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &ictl[td.x].status, mx, my); break;
+            case 5: oe2d_tile<T, 5, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &ictl[td.x].status, mx, my); break;
+            default: oe2d_tile<T, 6, PH, TX, TY>(tile, fc, sp, Uo, geo, ph, oe_type, gk, 1, dt_idx, dt_idy, td.y, td.z, nullptr, &ictl[td.x].status, mx, my); break;
           }
           mx = block_max<NT>(mx, red);
           my = block_max<NT>(my, red + 32);
@@ -160,8 +164,9 @@ __global__ void __launch_bounds__(TX * TY, 1)
         const double ax = __longlong_as_double((long long)c.alpha_bits);
         const double ay = __longlong_as_double((long long)c.alpha_bits_y);
         double dt = cfl / (ax / inst[i].dx + ay / inst[i].dy);
-        if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; atomicOr(&g->status, kStatusNonFinite); }
+        if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; c.status |= kStatusNonFinite; }
         c.dt = dt;
+        close_instance_step(c, &g->status);
       }
       c.alpha_bits = 0ull;
       c.alpha_bits_y = 0ull;

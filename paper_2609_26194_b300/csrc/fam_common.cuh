@@ -45,6 +45,10 @@ struct FamCtl {
   unsigned long long t1_maxabs_bits[4];
   unsigned long long t1_dev_bits[4];
   double t1_mean[4];
+  // face quadrature points at which a Rusanov trace had no spectral radius
+  // (NaN |v_n| + c: an Euler trace with gamma p / rho < 0), summed over the
+  // residual evaluations since the state was set
+  unsigned long long ntrace;
 };
 
 // Padded structure-of-arrays layout.  Plane p = c * nmom + m; within a
@@ -227,6 +231,18 @@ __device__ __forceinline__ bool less_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);
 }
 __device__ __forceinline__ bool less_nonneg(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+// isnan on the bit pattern (integer compare)
+__device__ __forceinline__ bool nan_bits(double v) {
+  return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool nan_bits(float v) { return (__float_as_int(v) & 0x7FFFFFFF) > 0x7F800000; }
+// Add a per-thread count to *counter (nullptr: no counting) with one atomic
+// per warp that has a non-zero sum; every lane of the warp must call it.
+__device__ __forceinline__ void warp_count_add(unsigned long long* counter, unsigned n) {
+  if (counter == nullptr) return;
+  const unsigned tot = __reduce_add_sync(0xffffffffu, n);
+  if ((threadIdx.x & 31) == 0 && tot != 0u) atomicAdd(counter, (unsigned long long)tot);
+}
 // isfinite on the exponent field (integer compare instead of an FP64 one)
 __device__ __forceinline__ bool finite_bits(double v) {
   return (__double_as_longlong(v) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;

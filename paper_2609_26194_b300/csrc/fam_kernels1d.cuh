@@ -51,10 +51,12 @@ __device__ __forceinline__ void coef1d(const T* tile, int c, int hx, T* cf) {
 // One stage on a tile already staged in shared memory: tile = the NP planes
 // of cells x0-2 .. x0+TX+1 (padded columns x0 .. x0+TX+3).  U0 / Uout point
 // at the instance's plane 0.  Called by all TX threads of the block.
+// ntrace (may be null) accumulates the faces of this tile at which a trace
+// has no spectral radius; each face of the grid is counted by one tile only.
 template <typename T, int K, class PH, int TX>
 __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const T* __restrict__ U0,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const T dt,
-                                             const int stage, const int x0) {
+                                             const int stage, const int x0, unsigned long long* ntrace) {
   constexpr int NC = PH::NC;
   constexpr int HX = TX + 4;
   constexpr int D = K - 1;
@@ -95,6 +97,7 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
     }
   }
   __syncthreads();
+  unsigned nbad = 0;
   for (int f = tx; f <= TX; f += TX) {
     T uL[NC], uR[NC], FL[NC], FR[NC];
 #pragma unroll
@@ -103,7 +106,10 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
     const T a = rusanov_speed(sL, sR);
 #pragma unroll
     for (int c = 0; c < NC; ++c) fL[f * NC + c] = T(0.5) * (FL[c] + FR[c]) - T(0.5) * a * (uR[c] - uL[c]);
+    // owner: the tile of the face's right cell (the grid's last face: its left cell's)
+    if ((nan_bits(sL) || nan_bits(sR)) && x0 + f <= geo.nx && (f < TX || x0 + f == geo.nx)) ++nbad;
   }
+  warp_count_add(ntrace, nbad);
   __syncthreads();
   const int i = x0 + tx;
   if (i >= geo.nx) return;  // no barrier follows
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(TX)
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;
-  stage1d_tile<T, K, PH, TX>(tile, fL, fR, U0, Uout, geo, ph, T(dtd), stage, x0);
+  stage1d_tile<T, K, PH, TX>(tile, fL, fR, U0, Uout, geo, ph, T(dtd), stage, x0, &ctl->ntrace);
 }
 
 // OE on a staged tile (layout as for stage1d_tile); returns this thread's

@@ -164,11 +164,14 @@ struct U0FromGlobal {
 // the TX x TY tile at (x0, y0), whose cells and 2-cell halo of every plane
 // are in shared memory at `tile` (HY x HX per plane).  xL, xR, yB, yT are the
 // face-trace / flux slots of Smem2D.  u0src supplies U^n for stages 2 and 3
-// (ready() is called once by every thread before phase C).
+// (ready() is called once by every thread before phase C).  ntrace (may be
+// null) accumulates the face points of this tile at which a trace has no
+// spectral radius; each face of the grid is counted by one tile only.
 template <typename T, int K, class PH, int TX, int TY, class U0Src>
 __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, T* xR, T* yB, T* yT,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const int stage,
-                                             const T dt, const int x0, const int y0, const U0Src& u0src) {
+                                             const T dt, const int x0, const int y0, const U0Src& u0src,
+                                             unsigned long long* ntrace) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int HX = S::HX, HY = S::HY;
@@ -306,6 +309,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   // ---- phase B: Rusanov fluxes at every face Gauss point -----------------
   // face point it: x-faces first (it = g * NFX + face), then y-faces
   constexpr int NXP = NFX * 4, NYP = NFY * 4;
+  unsigned nbad = 0;  // owned face points with a trace that has no spectral radius
   for (int it = threadIdx.x; it < NXP + NYP; it += NT) {
     T uL[NC], uR[NC], fL[NC], fR[NC];
     T* slot;
@@ -336,7 +340,25 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     const T a = rusanov_speed(sL, sR);
 #pragma unroll
     for (int c = 0; c < NC; ++c) slot[c * cs] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
+    if (nan_bits(sL) || nan_bits(sR)) {
+      // the face's owner: the tile holding the cell to its right (top), or
+      // for the grid's last face the tile to its left (bottom)
+      bool own;
+      if (it < NXP) {
+        const int f = it - (it / NFX) * NFX;
+        const int row = f < TX * TY ? f / TX : f - TX * TY, col = f < TX * TY ? f % TX : TX;
+        const int F = x0 + col;
+        own = y0 + row < geo.ny && F <= geo.nx && (col < TX || F == geo.nx);
+      } else {
+        const int q = it - NXP, f = q - (q / NFY) * NFY;
+        const int row = f / TX, col = f % TX;
+        const int F = y0 + row;
+        own = x0 + col < geo.nx && F <= geo.ny && (row < TY || F == geo.ny);
+      }
+      nbad += own ? 1u : 0u;
+    }
   }
+  warp_count_add(ntrace, nbad);
   __syncthreads();
 
   // ---- phase C: residual (eq. 11), Shu--Osher combination, store ---------
@@ -448,7 +470,7 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   }
 
   const U0FromSmem<T, TX, TY> u0src{u0s, bar + 1, ctl, want_u0};
-  stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, dt, x0, y0, u0src);
+  stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, dt, x0, y0, u0src, &ctl->ntrace);
 }
 
 // ---------------------------------------------------------------------------

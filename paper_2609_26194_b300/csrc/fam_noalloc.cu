@@ -15,7 +15,10 @@
 // call made on that device -- so the first call on a device should come
 // before any stream capture.  Every call shares the array and overwrites it:
 // calls whose GPU work overlaps (different streams, or different host
-// threads) race on it and must be serialised by the caller.
+// threads) race on it and must be serialised by the caller.  Each call
+// starts the control block from zero with a one-thread kernel and, at the
+// end, waits for its stream and reads the control block back to report the
+// step size and the device flags.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -57,6 +60,10 @@ cudaError_t scratch_address(void** out) {
   *out = g_scratch_dev[dev];
   return cudaSuccess;
 }
+
+// Start the control block of a call from `init` (passed by value: no host
+// buffer has to outlive the launch).
+__global__ void noalloc_ctl_reset(FamCtl* ctl, const FamCtl init) { *ctl = init; }
 
 }  // namespace
 
@@ -124,7 +131,8 @@ extern "C" fam_status fam_step1d_noalloc(const void* U_in, void* U_out, int nx, 
   c.dy = 1.0;
   c.dxe = g.dx;
   c.dye = 1.0;
-  if (cudaMemcpyAsync(h.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h.stream) != cudaSuccess) return FAM_E_CUDA;
+  noalloc_ctl_reset<<<1, 1, 0, h.stream>>>(h.ctl, c);
+  if (cudaGetLastError() != cudaSuccess) return FAM_E_CUDA;
   // input -> padded buffer A (+ ghost images)
   const size_t row = (size_t)nx * h.elem;
   for (int q = 0; q < h.np; ++q) {
@@ -144,14 +152,14 @@ extern "C" fam_status fam_step1d_noalloc(const void* U_in, void* U_out, int nx, 
     char* d0 = reinterpret_cast<char*>(U_out) + (size_t)q * row;
     if (cudaMemcpyAsync(d0, s0, row, cudaMemcpyDeviceToDevice, h.stream) != cudaSuccess) return FAM_E_CUDA;
   }
-  if (dt_used) {
-    // the step size of this step is the one the OE epilogue advanced the clock by
-    FamCtl out;
-    if (cudaMemcpyAsync(&out, h.ctl, sizeof(out), cudaMemcpyDeviceToHost, h.stream) != cudaSuccess) return FAM_E_CUDA;
-    if (cudaStreamSynchronize(h.stream) != cudaSuccess) return FAM_E_CUDA;
-    *dt_used = out.t;
-    if (out.status & (kStatusNonFinite | kStatusNonPhysical)) return FAM_E_NONPHYSICAL;
-    if (out.status & kStatusTimeout) return FAM_E_TIMEOUT;
-  }
+  // Every call waits for its step and reads the device flags, so that a
+  // non-physical or timed-out step is never reported as FAM_OK.  The step
+  // size taken is the one the OE epilogue advanced the clock by.
+  FamCtl out;
+  if (cudaMemcpyAsync(&out, h.ctl, sizeof(out), cudaMemcpyDeviceToHost, h.stream) != cudaSuccess) return FAM_E_CUDA;
+  if (cudaStreamSynchronize(h.stream) != cudaSuccess) return FAM_E_CUDA;
+  if (dt_used) *dt_used = out.t;
+  if (out.status & kStatusTimeout) return FAM_E_TIMEOUT;
+  if (out.status & (kStatusNonFinite | kStatusNonPhysical)) return FAM_E_NONPHYSICAL;
   return FAM_OK;
 }

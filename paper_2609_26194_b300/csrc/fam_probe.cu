@@ -79,22 +79,20 @@ extern "C" fam_status fam_alu_peak(int precision, double* flops_per_s) {
 extern "C" fam_status fam_selftest_math(const double* x_host, int n, double* rcp_host, double* rsqrt_host,
                                         double* sqrt_host) {
   if (!x_host || n <= 0 || !rcp_host || !rsqrt_host || !sqrt_host) return FAM_E_INVAL;
-  double *x, *a, *b, *c;
-  size_t bytes = sizeof(double) * (size_t)n;
-  if (cudaMalloc(&x, bytes) != cudaSuccess) return FAM_E_NOMEM;
-  cudaMalloc(&a, bytes);
-  cudaMalloc(&b, bytes);
-  cudaMalloc(&c, bytes);
-  cudaMemcpy(x, x_host, bytes, cudaMemcpyHostToDevice);
-  math_kernel<<<(n + 255) / 256, 256>>>(x, n, a, b, c);
-  cudaError_t e = cudaDeviceSynchronize();
-  cudaMemcpy(rcp_host, a, bytes, cudaMemcpyDeviceToHost);
-  cudaMemcpy(rsqrt_host, b, bytes, cudaMemcpyDeviceToHost);
-  cudaMemcpy(sqrt_host, c, bytes, cudaMemcpyDeviceToHost);
-  cudaFree(x);
-  cudaFree(a);
-  cudaFree(b);
-  cudaFree(c);
+  const size_t bytes = sizeof(double) * (size_t)n;
+  // one checked allocation, sliced: no kernel runs unless all of it exists
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, 4 * bytes) != cudaSuccess) return FAM_E_NOMEM;
+  double *x = buf, *a = buf + n, *b = buf + 2 * (size_t)n, *c = buf + 3 * (size_t)n;
+  cudaError_t e = cudaMemcpy(x, x_host, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    math_kernel<<<(n + 255) / 256, 256>>>(x, n, a, b, c);
+    e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(rcp_host, a, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(rsqrt_host, b, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(sqrt_host, c, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
   return e == cudaSuccess ? FAM_OK : FAM_E_CUDA;
 }
 
@@ -104,11 +102,13 @@ extern "C" fam_status fam_selftest_int_fp64(const double* a_host, const double* 
   double* buf = nullptr;
   if (cudaMalloc(&buf, 3 * bytes) != cudaSuccess) return FAM_E_NOMEM;
   double *a = buf, *b = buf + n, *p = buf + 2 * (size_t)n;
-  cudaMemcpy(a, a_host, bytes, cudaMemcpyHostToDevice);
-  cudaMemcpy(b, b_host, bytes, cudaMemcpyHostToDevice);
-  int_fp64_kernel<<<(n + 255) / 256, 256>>>(a, b, n, p);
-  cudaError_t e = cudaDeviceSynchronize();
-  cudaMemcpy(prod_host, p, bytes, cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(a, a_host, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b, b_host, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    int_fp64_kernel<<<(n + 255) / 256, 256>>>(a, b, n, p);
+    e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(prod_host, p, bytes, cudaMemcpyDeviceToHost);
   cudaFree(buf);
   return e == cudaSuccess ? FAM_OK : FAM_E_CUDA;
 }

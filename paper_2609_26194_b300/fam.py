@@ -32,7 +32,7 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
            "fam_batch_last_error", "fam_batch_destroy", "fam_batch2d_create", "fam_batch_tile",
            "fam_step1d_noalloc", "fam_adjoint",
-           "fam_run_fixed", "fam_set_bc", "fam_tune")
+           "fam_run_fixed", "fam_set_bc", "fam_tune", "fam_nonphysical_traces", "fam_batch_health")
 
 
 class FamError(RuntimeError):
@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
         L.fam_run_fixed.argtypes = [vp, l, dp]
         L.fam_set_bc.argtypes = [vp, i, i, dp]
         L.fam_tune.argtypes = [vp, d, i, ctypes.c_char_p, ctypes.POINTER(i)]
+        L.fam_nonphysical_traces.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.fam_last_error.argtypes = [vp]
         L.fam_last_error.restype = ctypes.c_char_p
         L.fam_status_string.argtypes = [i]
@@ -216,6 +217,13 @@ class Solver:
         t, dt, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_long()
         self._check(lib().fam_time(self._h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(s)))
         return t.value, dt.value, s.value
+
+    def nonphysical_traces(self) -> int:
+        """Face quadrature points whose Rusanov trace had no spectral radius,
+        summed over the residual evaluations since set_state()."""
+        n = ctypes.c_ulonglong()
+        self._check(lib().fam_nonphysical_traces(self._h, ctypes.byref(n)))
+        return n.value
 
     def profile(self) -> tuple[list, int]:
         """(ms per kernel [stage1, stage2, stage3, oe], profiled steps)."""
@@ -384,6 +392,15 @@ class Batch:
         self._check(lib().fam_batch_times(self._h, t.ctypes.data_as(dp), dt.ctypes.data_as(dp), st))
         return t, dt, np.array(st[:], dtype=np.int64)
 
+    def health(self):
+        """Per instance: (trace counts, status codes, first flagged step)."""
+        nt = (ctypes.c_ulonglong * self.n)()
+        st = (ctypes.c_int * self.n)()
+        bs = (ctypes.c_long * self.n)()
+        self._check(lib().fam_batch_health(self._h, nt, st, bs))
+        return (np.array(nt[:], dtype=np.int64), np.array(st[:], dtype=np.int32),
+                np.array(bs[:], dtype=np.int64))
+
     def info(self) -> dict:
         tx, g, nt, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_long(), ctypes.c_long()
         self._check(lib().fam_batch_info(self._h, ctypes.byref(tx), ctypes.byref(g), ctypes.byref(nt),
@@ -420,13 +437,14 @@ def _batch_sigs(L):
     L.fam_batch_times.argtypes = [vp, dp, dp, ctypes.POINTER(l)]
     L.fam_batch_info.argtypes = [vp, ip, ip, ctypes.POINTER(l), ctypes.POINTER(l)]
     L.fam_batch_tune.argtypes = [vp, d, i, ctypes.c_char_p, ip, ip]
+    L.fam_batch_health.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), ip, ctypes.POINTER(l)]
     L.fam_batch_last_error.argtypes = [vp]
     L.fam_batch_last_error.restype = ctypes.c_char_p
     L.fam_batch_destroy.argtypes = [vp]
     L.fam_batch_destroy.restype = None
     for name in ("fam_batch_create", "fam_batch2d_create", "fam_batch_set_option", "fam_batch_set_state",
                  "fam_batch_get_state", "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info",
-                 "fam_batch_tune", "fam_batch_tile"):
+                 "fam_batch_tune", "fam_batch_tile", "fam_batch_health"):
         getattr(L, name).restype = ctypes.c_int
     _batch_ready = True
 
@@ -438,14 +456,35 @@ def step1d_noalloc(U_in, U_out, nx: int, k: int, x0: float = 0.0, x1: float = 1.
     (ncomp, 2, nx), float64 or float32) without any device allocation by the
     library: its intermediate states live in a fixed static device array
     (at most FAM_NOALLOC_MAX_CELLS = 16384 cells).  Calls share that array,
-    so calls whose GPU work may overlap must be serialised by the caller."""
+    so calls whose GPU work may overlap must be serialised by the caller.
+    The call waits for its step and raises on a non-physical state.  stream
+    defaults to torch's current stream."""
+    ncomp = 3 if equation == EULER else 1
+    for name, t in (("U_in", U_in), ("U_out", U_out)):
+        if not _is_torch(t) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if tuple(t.shape) != (ncomp, 2, int(nx)):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {(ncomp, 2, int(nx))}")
+        if str(t.dtype) not in ("torch.float64", "torch.float32"):
+            raise TypeError(f"{name} must be float64 or float32")
+    if U_in.dtype != U_out.dtype:
+        raise TypeError("U_in and U_out differ in dtype")
+    if U_in.device != U_out.device:
+        raise ValueError("U_in and U_out are on different devices")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(U_in.device).cuda_stream
     L = lib()
     _noalloc_sig(L)
     prec = 64 if str(U_in.dtype) == "torch.float64" else 32
     dt = ctypes.c_double()
-    rc = L.fam_step1d_noalloc(ctypes.c_void_p(U_in.data_ptr()), ctypes.c_void_p(U_out.data_ptr()), int(nx),
-                              float(x0), float(x1), int(k), int(equation), int(bc), float(gamma), prec, float(cfl),
-                              ctypes.byref(dt) if return_dt else None, ctypes.c_void_p(stream or 0))
+    import torch
+    with torch.cuda.device(U_in.device):
+        rc = L.fam_step1d_noalloc(ctypes.c_void_p(U_in.data_ptr()), ctypes.c_void_p(U_out.data_ptr()), int(nx),
+                                  float(x0), float(x1), int(k), int(equation), int(bc), float(gamma), prec,
+                                  float(cfl), ctypes.byref(dt) if return_dt else None, ctypes.c_void_p(stream))
     if rc != 0:
         raise FamError(rc, "fam_step1d_noalloc failed")
     return dt.value if return_dt else None
