@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tile", default="auto", choices=["auto", "0", "1", "2"],
                     help="2D tile shape: the autotuner's pick, or an index into fam.TILES_2D")
+    ap.add_argument("--fused", default="0", choices=["0", "1"],
+                    help="with a fixed --tile: 1 runs the final stage and the OE as one fused launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-plain report")
@@ -306,7 +308,41 @@ def batched_report(a, torch):
                              "peak_gbs": hbm, "frac": 128.0 * bv / 1e9 / hbm},
             "speedup_vs_plain": bv / pv, "all_instances_advanced": bool(np.all(steps == a.batched_steps)),
             "status": status,
-            "dt_spread": [float(np.min(dts)), float(np.max(dts))]}
+            "dt_spread": [float(np.min(dts)), float(np.max(dts))],
+            "printed_ranges": batched_printed_ranges(a, nx, ks)}
+
+
+def batched_printed_ranges(a, nx, ks):
+    """The same instance sizes and orders with the Riemann generator at the
+    shock workload's printed ranges (rho [0.1, 2], |u| <= 1, p [0.1, 10]).
+    Without a positivity limiter some instances reach a non-physical state:
+    each one stops after that step while the others go on.  Reported: how
+    many completed, where the others stopped, and the face points whose
+    Rusanov trace had no spectral radius."""
+    from paper_2609_26194_b300 import fam, inputs
+    states = [inputs.euler1d_riemann(n, seed=4 + i, rho=(0.1, 2.0), umax=1.0, p=(0.1, 10.0))
+              for i, n in enumerate(nx)]
+    b = fam.Batch(nx, ks, bc=fam.OUTFLOW)
+    b.set_state(states)
+    t0 = time.perf_counter()
+    b.run(a.batched_steps, 0.3)
+    try:
+        b.sync()
+        status = "ok"
+    except fam.FamError as e:
+        status = str(e)
+    sec = time.perf_counter() - t0
+    ntr, st, bad = b.health()
+    _, _, steps = b.times()
+    b.close()
+    stopped = bad > 0
+    return {"rho": [0.1, 2.0], "umax": 1.0, "p": [0.1, 10.0], "steps": a.batched_steps, "status": status,
+            "completed": int(np.sum(~stopped)), "stopped": int(np.sum(stopped)),
+            "stop_step_quartiles": ([int(v) for v in np.percentile(bad[stopped], [0, 25, 50, 75, 100])]
+                                    if stopped.any() else []),
+            "nonphysical_traces": int(np.sum(ntr)),
+            "instances_with_nonphysical_traces": int(np.sum(ntr > 0)),
+            "cell_stages": int(3 * np.sum(np.asarray(nx) * steps)), "seconds": sec}
 
 
 def batched2d_report(a, torch):
@@ -367,8 +403,17 @@ def batched2d_report(a, torch):
                        "tiles": info["tiles"], "blocks_per_sm": bps, "kernel_launches": 1},
             "plain_loop": {"value": pv, "unit": UNIT, "steps": plain_steps, "seconds": plain_s,
                            "kernel_launches": 4 * len(nx) * plain_steps},
+            "hbm_roofline": {"algorithmic_bytes_per_cell_stage": 256.0, "achieved_gbs": 256.0 * bv / 1e9,
+                             "peak_gbs": _hbm_peak(), "frac": 256.0 * bv / 1e9 / _hbm_peak()},
             "speedup_vs_plain": bv / pv, "all_instances_advanced": bool(np.all(steps == nsteps)),
             "status": status}
+
+
+def _hbm_peak() -> float:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0
 
 
 def configs_report(a, torch):
@@ -434,8 +479,49 @@ def configs_report(a, torch):
                 out[f"euler2d_{name}_4096_k{k}_f{prec}"] = {"value": 3.0 * n * n * steps / sec, "seconds": sec,
                                                             "steps": steps, "tile": list(tile)}
             s.close()
+    # 2D Euler 4096^2, k = 5, FP32: the bench workload in single precision
+    st = torch.cuda.Stream()
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC, precision=32, stream=st.cuda_stream)
+    U32 = data["smooth"].astype(np.float32)
+    s.set_state(U32)
+    tile = fam.TILES_2D[s.tune(0.55, probe_steps=1)]
+    s.set_state(U32)
+    s.run_steps(steps, 0.55)
+    s.set_state(U32)
+    sec = timed(s, st, lambda: s.run_steps(steps, 0.55))
+    out["euler2d_smooth_4096_k5_f32"] = {"value": 3.0 * n * n * steps / sec, "seconds": sec, "steps": steps,
+                                         "tile": list(tile)}
+    s.close()
     return {"unit": UNIT, "note": "each run: CUDA events around one graph-captured multi-step launch "
-                                  "(after an untimed run of the same length)", "runs": out}
+                                  "(after an untimed run of the same length)", "runs": out,
+            "rectangles_printed_ranges": printed_rectangles_report(torch)}
+
+
+def printed_rectangles_report(torch, n: int = 4096, max_steps: int = 20):
+    """The rectangle workload at its printed ranges (rho, p in [0.1, 5],
+    |u|, |v| <= 1), 4096^2, k = 4 and 6, FP64: stepped one step at a time
+    until the state is flagged non-physical (no positivity limiter is built)
+    or max_steps pass; reports where it stopped and the face points whose
+    Rusanov trace had no spectral radius up to then (not a throughput)."""
+    from paper_2609_26194_b300 import fam, inputs
+    U = inputs.euler2d_rectangles(n, seed=3, nrect=64)
+    out = {}
+    for k in (4, 6):
+        cfl = 0.4 if k == 4 else 0.55
+        s = fam.Solver(2, n, n, k=k, equation=fam.EULER, bc=fam.PERIODIC, precision=64)
+        s.set_state(U)
+        status, done = "completed", max_steps
+        for q in range(1, max_steps + 1):
+            s.step(cfl)
+            try:
+                s.sync()
+            except fam.FamError as e:
+                status, done = f"{e} after step {q}", q
+                break
+        out[f"k{k}_f64"] = {"status": status, "steps": done, "nonphysical_traces": s.nonphysical_traces(),
+                            "face_points_per_step": 3 * 2 * n * (n + 1) * 4}
+        s.close()
+    return out
 
 
 def configs_report_safe(a, torch):
@@ -515,12 +601,16 @@ def run_fam(a):
     dev = torch.from_numpy(U).cuda()
     s.set_state(dev)
     # the library's tile autotuner (a few probe steps per tile shape, untimed)
+    # (and whether the final stage and the OE run split or as one fused launch)
     if a.tile == "auto":
         tile = fam.TILES_2D[s.tune(cfl, probe_steps=2)]
+        fused = s.fused_oe
         s.set_state(dev)
     else:
         s.set_option("tile2d", int(a.tile))
         tile = fam.TILES_2D[int(a.tile)]
+        fused = int(a.fused)
+        s.set_option("fused_oe", fused)
     for _ in range(a.warmup):
         s.step(cfl)
     s.sync()
@@ -560,10 +650,15 @@ def run_fam(a):
     e2e = {"value": world * 3.0 * cells * a.e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
 
-    # roofline of the dominant kernel (the stage kernel)
+    # roofline of the dominant kernel (the stage kernel; with the fused final
+    # stage + OE, stages 1 and 2 are the plain stage kernel's launches)
     peak_flops = fam.alu_peak(prec)
-    stage_ms = sum(kern_ms[:3]) / max(1, 3 * prof_steps)
-    oe_ms = kern_ms[3] / max(1, prof_steps)
+    if fused:
+        stage_ms = sum(kern_ms[:2]) / max(1, 2 * prof_steps)
+        oe_ms = None
+    else:
+        stage_ms = sum(kern_ms[:3]) / max(1, 3 * prof_steps)
+        oe_ms = kern_ms[3] / max(1, prof_steps)
     fpc = FLOP_PER_CELL_STAGE.get((k, prec))
     traffic = DRAM_BYTES_PER_CELL.get((k, prec))
     if fpc is not None:
@@ -590,12 +685,14 @@ def run_fam(a):
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32",
             "data": "synthetic (seeded analytic initial data, exact moments)",
-            "config": {**workload_config(a), "tile": list(tile),
+            "config": {**workload_config(a), "tile": list(tile), "final_stage_and_oe": "fused" if fused else "split",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "hbm_roofline": hbm_roof,
-            "kernel_ms": {"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
-                          "stage3": kern_ms[2] / max(1, prof_steps), "oe": oe_ms},
-            "e2e": e2e, "gpu_launches": 4 * a.steps, "clocks": ck}
+            "kernel_ms": ({"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
+                           "stage3_oe_fused": kern_ms[2] / max(1, prof_steps)} if fused else
+                          {"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
+                           "stage3": kern_ms[2] / max(1, prof_steps), "oe": oe_ms}),
+            "e2e": e2e, "gpu_launches": (3 if fused else 4) * a.steps, "clocks": ck}
     if rank == 0 and world == 1 and not a.no_batched:
         line["batched"] = batched_report(a, torch)
         line["batched2d"] = batched2d_report(a, torch)

@@ -87,6 +87,14 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
  *   "dt_max"     upper bound on the step size (<= 0: none)
  *   "tile2d"     2D tile shape of the stage / OE kernels: 0 = 32 x 8 (default),
  *                1 = 32 x 4, 2 = 16 x 8 cells (see fam_tune)
+ *   "fused_oe"   2D only: 1 runs the final RK stage and the OE in one
+ *                persistent launch (not in the paper: tiles of the final
+ *                stage and, once the tiles around them are done, the OE of
+ *                each tile, taken from an ordered task list; the final stage's
+ *                output stays in L2 between the two); 0 (default) runs them
+ *                as two kernels.  Results agree to rounding; Type-I OE
+ *                (grid-wide statistics of the final stage) always runs split.
+ *                fam_tune chooses it per problem
  *   "profile"    1: fam_step() brackets each of its four kernel launches with
  *                CUDA events (read with fam_profile); setting it resets the
  *                accumulated times
@@ -137,11 +145,13 @@ fam_status fam_run(fam_t h, double T, double cfl, long max_steps, long* nsteps_o
 fam_status fam_run_fixed(fam_t h, long nsteps, const double* dts);
 
 /* Autotuner (not in the paper): times probe_steps steps of each 2D tile
- * shape on the handle's current state (restored afterwards, clock included),
- * keeps the fastest and appends it to cache_path (if not NULL) keyed by GPU
- * name, equation, order, precision and grid; a cached entry is reused
- * without timing.  *choice (may be NULL) receives the "tile2d" index.  1D
- * handles have one shape (choice 0).  Synchronous. */
+ * shape, with the final stage and OE split and fused (option "fused_oe";
+ * split only for Type-I OE), on the handle's current state (restored
+ * afterwards, clock included), keeps the fastest and appends it to
+ * cache_path (if not NULL) keyed by GPU name, equation, order, precision
+ * and grid; a cached entry is reused without timing.  *choice (may be NULL)
+ * receives tile2d + 3 * fused_oe (0..5).  1D handles have one shape and no
+ * fused path (choice 0).  Synchronous. */
 fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path, int* choice);
 
 /* Wait for the handle's stream and report device-side status flags. */
@@ -153,8 +163,9 @@ fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps);
 
 /* Per-kernel device time accumulated over the profiled fam_step() calls since
  * the option "profile" was last set: ms[0..2] = stage 1..3 kernels, ms[3] =
- * OE kernel (milliseconds, CUDA events on the handle's stream); *nsteps =
- * number of profiled steps.  Synchronises the stream. */
+ * OE kernel (milliseconds, CUDA events on the handle's stream); with
+ * "fused_oe", ms[2] holds the fused final stage + OE launch and ms[3] is 0;
+ * *nsteps = number of profiled steps.  Synchronises the stream. */
 fam_status fam_profile(fam_t h, double* ms, long* nsteps);
 
 /* Number of face quadrature points (1D: faces) at which one of the two

@@ -557,10 +557,12 @@ static double default_gamma_k(const or_problem* P) {
 }
 
 /* Type-II denominator D and tolerance eps over the stencil Lambda of averages
- * vals[0..n-1] (Tab. sigma1d / sigma2d; S_Lambda is the unnormalised sum). */
-static void type2_den(const double* vals, int n, double* D, double* eps) {
+ * vals[0..n-1] (Tab. sigma1d / sigma2d; S_Lambda is the unnormalised sum, as
+ * printed; mean != 0 selects the alternative reading S_Lambda / |Lambda|). */
+static void type2_den(const double* vals, int n, int mean, double* D, double* eps) {
   double S = 0.0, mabs = 0.0, d = 0.0;
   for (int q = 0; q < n; ++q) S += vals[q];
+  if (mean) S /= (double)n;
   for (int q = 0; q < n; ++q) {
     double t = fabs(vals[q] - S);
     if (t > d) d = t;
@@ -623,7 +625,7 @@ int or_oe(const or_problem* P, double dt, double* U, double* theta) {
           eps = eO[c];
         } else {
           double v[3] = {*pv(&A, c, 0, 0, i - 1), *pv(&A, c, 0, 0, i), *pv(&A, c, 0, 0, i + 1)};
-          type2_den(v, 3, &D, &eps);
+          type2_den(v, 3, P->oe_mean, &D, &eps);
         }
         double s = (D < eps) ? 0.0 : gk * (fabs(jl) + fabs(jr)) / D;
         if (s > sig) sig = s;
@@ -671,7 +673,7 @@ int or_oe(const or_problem* P, double dt, double* U, double* theta) {
             double v[9];
             for (int s = 0; s < 3; ++s)
               for (int r = 0; r < 3; ++r) v[3 * s + r] = *pv(&A, c, 0, j - 1 + s, i - 1 + r);
-            type2_den(v, 9, &D, &eps);
+            type2_den(v, 9, P->oe_mean, &D, &eps);
           }
           double ssx = 0.0, ssy = 0.0;
           if (!(D < eps)) {

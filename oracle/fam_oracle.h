@@ -42,6 +42,8 @@ typedef struct {
   int oe_type;        /* OR_OE_NONE / OR_OE_TYPE1 / OR_OE_TYPE2 */
   double gamma_k;     /* OE constant; <= 0 selects the paper's default */
   int oe_jump_q6;     /* 2D k=6: 1 = jumps of full Q6 (printed matrices), 0 = of p6 */
+  int oe_mean;        /* Type II: 0 = S_Lambda the unnormalised sum (as printed),
+                         1 = the mean over Lambda (an alternative reading) */
 } or_problem;
 
 int or_ncomp(const or_problem* P);

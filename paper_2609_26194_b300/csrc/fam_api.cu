@@ -210,9 +210,76 @@ static fam_status enqueue_typeI(fam_handle* h, int b) {
   return FAM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// fused final stage + OE: task list of the persistent launch
+// ---------------------------------------------------------------------------
+// Stage tasks in row-major tile order; each OE task right after the last
+// stage task it waits for (the tiles whose cells or ghost images its 2-cell
+// halo reads, halo_tiles) plus twice the launch's resident block count, so
+// that the stage tasks it needs have most likely finished when it is taken.  The
+// fused path needs the Type-II (or no) OE: Type I reads grid-wide statistics
+// of the final stage, which exist only once every tile has finished.
+static void free_fused(fam_handle* h) {
+  if (h->fz_tasks) cudaFree(h->fz_tasks);
+  if (h->fz_sync) cudaFree(h->fz_sync);
+  h->fz_tasks = nullptr;
+  h->fz_sync = nullptr;
+  h->fz_ready = false;
+}
+
+static bool use_fused(const fam_handle* h) {
+  return h->fused_oe && h->d == 2 && h->oe_type != 1 && h->fz_ready && h->ops.fused;
+}
+
+static fam_status build_fused(fam_handle* h) {
+  if (!h->fused_oe || h->d != 2 || h->fz_ready) return FAM_OK;
+  if (!h->ops.fused) return fail(h, FAM_E_UNSUPPORTED, "no fused kernel for this configuration");
+  free_fused(h);
+  int dev = 0, sms = 0, per_sm = 0;
+  FAM_CUDA(h, cudaGetDevice(&dev));
+  FAM_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FAM_CUDA(h, h->ops.fused_occupancy(&per_sm));
+  if (per_sm < 1) return fail(h, FAM_E_UNSUPPORTED, "fused kernel does not fit on an SM");
+  const int TX = h->ops.tx, TY = h->ops.ty;
+  const int ntx = (h->geo.nx + TX - 1) / TX, nty = (h->geo.ny + TY - 1) / TY, nt = ntx * nty;
+  h->fz_grid = std::min(sms * per_sm, nt);
+  std::vector<std::vector<int>> after(nt);
+  const int* bc = h->geo.bc;
+  for (int ty = 0; ty < nty; ++ty)
+    for (int tx = 0; tx < ntx; ++tx) {
+      int cx[5], cy[5];
+      const int mx = halo_tiles(tx, TX, h->geo.nx, bc[0], bc[1], cx);
+      const int my = halo_tiles(ty, TY, h->geo.ny, bc[2], bc[3], cy);
+      int last = 0;
+      for (int b = 0; b < my; ++b)
+        for (int a = 0; a < mx; ++a) last = std::max(last, cy[b] * ntx + cx[a]);
+      after[std::min(nt - 1, last + 2 * h->fz_grid)].push_back(ty * ntx + tx);
+    }
+  std::vector<int> seq;
+  seq.reserve(2 * (size_t)nt);
+  for (int q = 0; q < nt; ++q) {
+    seq.push_back(q);
+    for (int t : after[q]) seq.push_back(nt + t);
+  }
+  FAM_CUDA(h, cudaMalloc(&h->fz_tasks, sizeof(int) * seq.size()));
+  FAM_CUDA(h, cudaMalloc(&h->fz_sync, sizeof(unsigned int) * (nt + 1)));
+  FAM_CUDA(h, cudaMemcpy(h->fz_tasks, seq.data(), sizeof(int) * seq.size(), cudaMemcpyHostToDevice));
+  h->fz_ntasks = (int)seq.size();
+  h->fz_ntiles = nt;
+  h->fz_ready = true;
+  return FAM_OK;
+}
+
+static fam_status enqueue_fused(fam_handle* h) {
+  FAM_CUDA(h, cudaMemsetAsync(h->fz_sync, 0, sizeof(unsigned int) * (h->fz_ntiles + 1), h->stream));
+  FAM_CUDA(h, h->ops.fused(h));
+  return FAM_OK;
+}
+
 static fam_status enqueue_step(fam_handle* h) {
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
+  if (use_fused(h)) return enqueue_fused(h);
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   fam_status s = enqueue_typeI(h, 1);
   if (s) return s;
@@ -241,6 +308,14 @@ static fam_status enqueue_step_profiled(fam_handle* h) {
   FAM_CUDA(h, cudaEventRecord(e[1], h->stream));
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   FAM_CUDA(h, cudaEventRecord(e[2], h->stream));
+  h->prof_fused.push_back(use_fused(h) ? 1 : 0);
+  if (use_fused(h)) {  // stage 3 and OE in one launch: all of it in ms[2], none in ms[3]
+    fam_status s = enqueue_fused(h);
+    if (s) return s;
+    FAM_CUDA(h, cudaEventRecord(e[3], h->stream));
+    FAM_CUDA(h, cudaEventRecord(e[4], h->stream));
+    return FAM_OK;
+  }
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   FAM_CUDA(h, cudaEventRecord(e[3], h->stream));
   fam_status s = enqueue_typeI(h, 1);
@@ -292,6 +367,8 @@ static fam_status ensure_dt(fam_handle* h, double cfl, double T) {
   {
     fam_status b = check_bc(h);
     if (b) return b;
+    b = build_fused(h);  // outside any stream capture: it allocates
+    if (b) return b;
   }
   if (!(cfl > 0.0)) return fail(h, FAM_E_INVAL, "cfl must be positive");
   if (!h->dt_valid || cfl != h->cfl_set || T != h->T_set) return refresh_dt(h, cfl, T, false);
@@ -324,6 +401,7 @@ void fam_destroy(fam_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  free_fused(h);
   for (int b = 0; b < 3; ++b)
     if (h->buf[b]) cudaFree(h->buf[b]);
   if (h->ctl) cudaFree(h->ctl);
@@ -430,6 +508,7 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
 static fam_status select_tile(fam_handle* h, int t) {
   FAM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->tile2d = t;
+  free_fused(h);  // the task list depends on the tile shape
   if (!pick(h)) return fail(h, FAM_E_UNSUPPORTED, "no kernels for this configuration");
   FAM_CUDA(h, h->ops.prepare());
   fam_status s = encode_maps(h);
@@ -465,9 +544,12 @@ fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path
         if (std::strcmp(line, key) == 0) {
           const int t = std::atoi(tab + 1);
           std::fclose(f);
-          if (t < 0 || t > 2) break;
+          if (t < 0 || t > 5 || (t > 2 && h->oe_type == 1)) break;
           if (choice) *choice = t;
-          return select_tile(h, t);
+          h->fused_oe = t / 3;
+          fam_status st = select_tile(h, t % 3);
+          if (st == FAM_OK) st = build_fused(h);
+          return st;
         }
       }
       std::fclose(f);
@@ -482,10 +564,16 @@ fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best = h->tile2d;
+  const int fused_was = h->fused_oe;
+  int best = h->tile2d + 3 * fused_was;
   float best_ms = 1e30f;
-  for (int t = 0; t < 3 && s == FAM_OK; ++t) {
+  // candidates: every tile shape, split and (Type II / no OE) fused
+  const int nfused = h->oe_type == 1 ? 1 : 2;
+  for (int cand = 0; cand < 3 * nfused && s == FAM_OK; ++cand) {
+    const int t = cand % 3;
     if (select_tile(h, t) != FAM_OK) continue;
+    h->fused_oe = cand / 3;
+    if (build_fused(h) != FAM_OK) continue;
     cudaMemcpyAsync(h->buf[0], save, sb, cudaMemcpyDeviceToDevice, h->stream);
     if (refresh_dt(h, cfl, 0.0, true) != FAM_OK) continue;
     enqueue_step(h);  // warm-up
@@ -499,12 +587,14 @@ fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      best = t;
+      best = cand;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  fam_status s2 = select_tile(h, best);
+  h->fused_oe = best / 3;
+  fam_status s2 = select_tile(h, best % 3);
+  if (s2 == FAM_OK) s2 = build_fused(h);
   cudaMemcpyAsync(h->buf[0], save, sb, cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(h->ctl, &ctl_save, sizeof(FamCtl), cudaMemcpyHostToDevice, h->stream);
   cudaStreamSynchronize(h->stream);
@@ -545,9 +635,15 @@ fam_status fam_set_option(fam_t h, const char* key, double v) {
     if (h->d != 2) return fail(h, FAM_E_INVAL, "tile2d applies to 2D grids");
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, FAM_E_INVAL, "tile2d must be 0, 1 or 2");
     return select_tile(h, (int)v);
+  } else if (k == "fused_oe") {
+    if (h->d != 2) return fail(h, FAM_E_INVAL, "fused_oe applies to 2D grids");
+    if (v != 0.0 && v != 1.0) return fail(h, FAM_E_INVAL, "fused_oe must be 0 or 1");
+    h->fused_oe = (int)v;
+    free_fused(h);
   } else if (k == "profile") {
     h->profile = v != 0.0;
     h->ev_used = 0;
+    h->prof_fused.clear();
     h->prof_steps = 0;
     for (double& x : h->prof_ms) x = 0.0;
     return FAM_OK;
@@ -599,6 +695,7 @@ fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state) {
   h->geo.bc[side] = bc;
   h->geo.bcx = h->geo.bc[0];
   h->geo.bcy = h->geo.bc[2];
+  free_fused(h);  // the fused task order follows the sides' ghost images
   if (bc == kBcInflow)
     for (int c = 0; c < h->nc; ++c) h->inflow[side][c] = inflow_state[c];
   fam_status s = fill_inflow(h);
@@ -684,7 +781,13 @@ fam_status fam_sync(fam_t h) {
   FamCtl c;
   fam_status s = ctl_read(h, &c);
   if (s) return s;
-  if (c.status & kStatusTimeout) return fail(h, FAM_E_TIMEOUT, "a kernel's bounded wait timed out");
+  if (c.status & kStatusTimeout) {
+    static const char* kinds[] = {"?", "tile copy", "U^n copy", "tile flag"};
+    char msg[200];
+    std::snprintf(msg, sizeof(msg), "a kernel's bounded wait timed out (%s; task %u, waited for %u, phase %u)",
+                  kinds[c.wait_where <= 3u ? c.wait_where : 0u], c.wait_task, c.wait_dep, c.wait_phase);
+    return fail(h, FAM_E_TIMEOUT, msg);
+  }
   if (c.status & (kStatusNonFinite | kStatusNonPhysical))
     return fail(h, FAM_E_NONPHYSICAL, (c.status & kStatusNonFinite) ? "non-finite state" : "non-physical state");
   return FAM_OK;
@@ -740,7 +843,8 @@ fam_status fam_profile(fam_t h, double* ms, long* nsteps) {
   if (!h || !ms) return FAM_E_INVAL;
   FAM_CUDA(h, cudaStreamSynchronize(h->stream));
   for (size_t b = 0; b + 5 <= h->ev_used; b += 5) {
-    for (int q = 0; q < 4; ++q) {
+    const bool fused = b / 5 < h->prof_fused.size() && h->prof_fused[b / 5];
+    for (int q = 0; q < (fused ? 3 : 4); ++q) {
       float t = 0.f;
       FAM_CUDA(h, cudaEventElapsedTime(&t, h->ev_pool[b + q], h->ev_pool[b + q + 1]));
       h->prof_ms[q] += t;
@@ -748,6 +852,7 @@ fam_status fam_profile(fam_t h, double* ms, long* nsteps) {
     h->prof_steps += 1;
   }
   h->ev_used = 0;
+  h->prof_fused.clear();
   for (int q = 0; q < 4; ++q) ms[q] = h->prof_ms[q];
   if (nsteps) *nsteps = h->prof_steps;
   return FAM_OK;

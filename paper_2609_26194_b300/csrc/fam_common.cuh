@@ -49,7 +49,26 @@ struct FamCtl {
   // (NaN |v_n| + c: an Euler trace with gamma p / rho < 0), summed over the
   // residual evaluations since the state was set
   unsigned long long ntrace;
+  // where the first bounded wait that gave up was (0: none): wait kind
+  // (kWait*), task or tile index, the tile waited for, mbarrier phase
+  unsigned int wait_where, wait_task, wait_dep, wait_phase;
 };
+
+enum : unsigned int {
+  kWaitTileCopy = 1u,   // TMA copy of a tile + halo
+  kWaitU0Copy = 2u,     // TMA copy of U^n rows
+  kWaitTileFlag = 3u,   // flag of a tile whose final stage an OE task needs
+};
+
+// Record the first wait that gave up (later ones keep the first record).
+__device__ __forceinline__ void note_wait(FamCtl* ctl, unsigned int where, unsigned int task, unsigned int dep,
+                                          unsigned int phase) {
+  if (atomicCAS(&ctl->wait_where, 0u, where) == 0u) {
+    ctl->wait_task = task;
+    ctl->wait_dep = dep;
+    ctl->wait_phase = phase;
+  }
+}
 
 // Padded structure-of-arrays layout.  Plane p = c * nmom + m; within a
 // plane, row r (r = j + G in 2D, 0 in 1D) and column q = i + G.
@@ -375,6 +394,22 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (TMA) writes to it (a TMA load reusing a buffer).
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Flags between CTAs of one launch: release store / acquire load at GPU scope.
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // ---------------------------------------------------------------------------

@@ -32,6 +32,10 @@ struct Ops {
   cudaError_t (*oe)(struct fam_handle*, int in, int out, double dt_override);
   cudaError_t (*alpha)(struct fam_handle*, int buf);
   cudaError_t (*prepare)();  // set shared-memory attributes
+  // 2D only (null in 1D): final stage + OE in one persistent launch (C -> B
+  // -> A with U^n = A), and the resident blocks per SM of that kernel
+  cudaError_t (*fused)(struct fam_handle*);
+  cudaError_t (*fused_occupancy)(int* blocks_per_sm);
 };
 
 struct fam_handle {
@@ -68,9 +72,17 @@ struct fam_handle {
   // the three stage launches and the OE launch of fam_step()
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
+  std::vector<char> prof_fused;  // per profiled step: stage 3 and OE ran fused
   size_t ev_used = 0;
   double prof_ms[4] = {0, 0, 0, 0};
   long prof_steps = 0;
+  // fused final stage + OE (option "fused_oe"): the task list of the
+  // persistent launch, its ticket / tile flags, and its grid size
+  int fused_oe = 0;
+  int* fz_tasks = nullptr;
+  unsigned int* fz_sync = nullptr;
+  int fz_ntasks = 0, fz_ntiles = 0, fz_grid = 0;
+  bool fz_ready = false;  // task list built for the current tile shape and sides
 };
 
 inline fam_status fail(fam_handle* h, fam_status s, const std::string& msg) {
@@ -124,12 +136,26 @@ template <typename T, int K, class PH, int TX2, int TY2>
 struct Impl2D {
   static constexpr int kTX = TX2, kTY = TY2;
   using S = Smem2D<T, PH::NC, TX2, TY2>;
+  using SF = SmemFused<T, PH::NC, TX2, TY2>;
   static cudaError_t prepare() {
     cudaError_t e = cudaFuncSetAttribute(stage2d<T, K, PH, TX2, TY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::bytes_stage);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(stage3_oe2d<T, K, PH, TX2, TY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SF::bytes);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(oe2d<T, K, PH, TX2, TY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)S::bytes_oe);
+  }
+  static cudaError_t fused_occupancy(int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, stage3_oe2d<T, K, PH, TX2, TY2>, TX2 * TY2,
+                                                         SF::bytes);
+  }
+  static cudaError_t fused(fam_handle* h) {
+    stage3_oe2d<T, K, PH, TX2, TY2><<<h->fz_grid, TX2 * TY2, SF::bytes, h->stream>>>(
+        bufp<T>(h, 2), bufp<T>(h, 0), bufp<T>(h, 1), bufp<T>(h, 0), h->geo, make_phys<T, PH>(h), h->ctl, h->oe_type,
+        T(default_gamma_k(h)), h->oe_q6, h->fz_tasks, h->fz_ntasks, h->fz_sync);
+    return cudaGetLastError();
   }
   static dim3 grid(const fam_handle* h) {
     return dim3((h->geo.nx + TX2 - 1) / TX2, (h->geo.ny + TY2 - 1) / TY2);
@@ -181,8 +207,10 @@ struct Impl1D {
   }
 };
 
-template <class I> Ops ops_of() { return Ops{0, 0, &I::stage, &I::oe, &I::alpha, &I::prepare}; }
-template <class I> Ops ops_of2d() { return Ops{I::kTX, I::kTY, &I::stage, &I::oe, &I::alpha, &I::prepare}; }
+template <class I> Ops ops_of() { return Ops{0, 0, &I::stage, &I::oe, &I::alpha, &I::prepare, nullptr, nullptr}; }
+template <class I> Ops ops_of2d() {
+  return Ops{I::kTX, I::kTY, &I::stage, &I::oe, &I::alpha, &I::prepare, &I::fused, &I::fused_occupancy};
+}
 
 // per-configuration selectors, one per instantiation unit (fam_inst.cu)
 #define FAM_DECL_PICK(D, P, K) bool fam_pick_d##D##_p##P##_k##K(fam_handle* h);

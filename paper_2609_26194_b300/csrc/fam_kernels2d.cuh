@@ -106,6 +106,7 @@ __device__ __forceinline__ bool load_tile(T* tile, uint64_t* bar, const CUtensor
   bool ok = mbar_wait(bar, 0);
   if (!ok) {
     atomicOr(&ctl->status, kStatusTimeout);
+    note_wait(ctl, kWaitTileCopy, blockIdx.x, blockIdx.y, 0u);
     mbar_wait(bar, 0);  // let an in-flight copy land before the block exits
   }
   return ok;
@@ -137,10 +138,12 @@ struct U0FromSmem {
   uint64_t* bar;
   FamCtl* ctl;
   bool want;
+  uint32_t phase = 0;  // mbarrier phase parity of this copy
   __device__ __forceinline__ bool ready() const {
-    if (want && !mbar_wait(bar, 0)) {
+    if (want && !mbar_wait(bar, phase)) {
       atomicOr(&ctl->status, kStatusTimeout);
-      mbar_wait(bar, 0);  // let an in-flight copy land before the block exits
+      note_wait(ctl, kWaitU0Copy, blockIdx.x, blockIdx.y, phase);
+      mbar_wait(bar, phase);  // let an in-flight copy land before the block exits
       return false;
     }
     return true;
@@ -157,6 +160,18 @@ struct U0FromGlobal {
   __device__ __forceinline__ bool ready() const { return true; }
   __device__ __forceinline__ T u0(const Geo& g, int p, int j, int i, int, int) const {
     return U0[cell_index(g, p, j, i)];
+  }
+};
+
+// U^n read at the cell through L2 only (fused final stage + OE: other blocks
+// of the launch write neighbouring cells of the same lines with U^{n+1}; this
+// tile's own cells are written only by its own OE task, after its stage task).
+template <typename T>
+struct U0FromL2 {
+  const T* U0;
+  __device__ __forceinline__ bool ready() const { return true; }
+  __device__ __forceinline__ T u0(const Geo& g, int p, int j, int i, int, int) const {
+    return __ldcg(U0 + cell_index(g, p, j, i));
   }
 };
 
@@ -670,6 +685,204 @@ __global__ void __launch_bounds__(TX * TY, 1)
     atomic_max_nonneg(&ctl->alpha_bits[1], (double)my);
     step_epilogue(ctl, gridDim.x * gridDim.y, true);
   }
+}
+
+// ---------------------------------------------------------------------------
+// final stage and OE fused into one persistent launch
+// ---------------------------------------------------------------------------
+// The OE of a tile (eq. 2dOE_sol) reads the final stage's output on the tile
+// and its 2-cell halo.  Instead of recomputing that stage on the halo (a
+// 1.5-1.8x larger stage for the tile shapes that fit), one launch walks a
+// task list: "stage" tasks run the final RK stage of a tile (stage2d_tile),
+// publish its output W and raise the tile's flag; "OE" tasks wait for the
+// flags of the tiles that wrote their halo, then run the OE of their tile
+// (oe2d_tile) from W, which is still in L2.  Both task kinds stage their tile
+// with L2-only vector loads (no TMA or mbarrier in this kernel).  The host orders the list so
+// that every OE task comes after the stage tasks it waits for; blocks take
+// tasks in list order from a ticket counter, so a waiting block only ever
+// waits for tasks already taken by running blocks (no deadlock, whatever the
+// grid size).  Every wait is bounded (kWaitLimitNs); a block that gives up
+// records kStatusTimeout, which makes the others stop taking tasks.
+
+// The interior cell whose value (or ghost image, written by the stage
+// kernels' store_with_ghosts) is found at cell c of a direction with n cells
+// and side conditions lo / hi; -1 for an inflow ghost (a fixed value).
+__host__ __device__ inline int halo_source(int c, int n, int lo, int hi) {
+  if (c >= 0 && c < n) return c;
+  if (c < 0) {
+    if (lo == kBcPeriodic) return c + n;
+    if (lo == kBcOutflow) return 0;
+    if (lo == kBcReflective) return -1 - c;
+    return -1;
+  }
+  if (hi == kBcPeriodic) return c - n;
+  if (hi == kBcOutflow) return n - 1;
+  if (hi == kBcReflective) return 2 * n - 1 - c;
+  return -1;
+}
+
+// Tile indices (along one direction, tiles of width TW) whose cells are read
+// by the OE of tile t through its 2-cell halo; returns how many (<= 5).
+__host__ __device__ inline int halo_tiles(int t, int TW, int n, int lo, int hi, int* out) {
+  int m = 0;
+  out[m++] = t;
+  const int x0 = t * TW, xe = (x0 + TW < n) ? x0 + TW : n;
+  const int cs[4] = {x0 - 2, x0 - 1, xe, xe + 1};
+  for (int q = 0; q < 4; ++q) {
+    const int src = halo_source(cs[q], n, lo, hi);
+    if (src < 0) continue;
+    const int o = src / TW;
+    bool seen = false;
+    for (int r = 0; r < m; ++r) seen = seen || out[r] == o;
+    if (!seen) out[m++] = o;
+  }
+  return m;
+}
+
+// Load the tile + halo box ((TX+4) x (TY+4) x NP at padded (x0, y0)) of W
+// with L2-only vector loads (W was written by other blocks of this launch, so
+// no line of it may come from this SM's L1); outside the padded planes: 0.
+template <typename T, int NP, int TX, int TY, int NT>
+__device__ __forceinline__ void load_tile_l2(T* tile, const T* __restrict__ W, const Geo& g, int x0, int y0) {
+  constexpr int HX = TX + 4, HY = TY + 4;
+  constexpr int VW = 16 / (int)sizeof(T);  // elements per 16-byte vector
+  constexpr int VR = HX / VW;              // vectors per row
+  static_assert(HX % VW == 0, "tile rows hold whole vectors");
+  for (int q = threadIdx.x; q < NP * HY * VR; q += NT) {
+    const int p = q / (HY * VR), r = q - p * (HY * VR);
+    const int y = y0 + r / VR, xv = x0 + (r % VR) * VW;
+    T* dst = tile + (size_t)p * HY * HX + (size_t)(r / VR) * HX + (r % VR) * VW;
+    // px is a multiple of 4 elements and xv of VW, so a vector is all in or all out
+    if (y < g.rows && xv < g.px) {
+      const T* src = W + (long long)p * g.plane + (long long)y * g.px + xv;
+      if constexpr (sizeof(T) == 8) {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(src));
+        dst[0] = v.x;
+        dst[1] = v.y;
+      } else {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
+        dst[0] = v.x;
+        dst[1] = v.y;
+        dst[2] = v.z;
+        dst[3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VW; ++e) dst[e] = T(0);
+    }
+  }
+}
+
+template <typename T, int NC, int TX, int TY>
+struct SmemFused {
+  using S = Smem2D<T, NC, TX, TY>;
+  static constexpr size_t bytes = S::bytes_stage > S::bytes_oe ? S::bytes_stage : S::bytes_oe;
+};
+
+template <typename T, int K, class PH, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
+    stage3_oe2d(const T* __restrict__ Win, const T* U0, T* __restrict__ W, T* Uout, const Geo geo, const PH ph,
+                FamCtl* __restrict__ ctl,
+                const int oe_type, const T gamma_k, const int q6, const int* __restrict__ tasks, const int ntasks,
+                unsigned int* __restrict__ tsync /* [0] ticket, [1 + t] flag of tile t */) {
+  constexpr int NC = PH::NC;
+  using S = Smem2D<T, NC, TX, TY>;
+  constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
+  constexpr int NT = TX * TY;
+  constexpr int RX = TX + 2, RY = TY + 2;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  // stage-task layout (as stage2d; U^n comes from L2 at the cell)
+  T* xL = tile + S::U0OFF + S::U0T;
+  T* xR = xL + S::XF;
+  T* yB = xR + S::XF;
+  T* yT = yB + S::YF;
+  // OE-task layout (as oe2d)
+  T* fc = tile + S::TILE;
+  T* sp = fc + 4 * NC * RX * RY;
+  __shared__ double red[64];
+  __shared__ int task_s, ok_s;
+
+  const double dtd = ctl->dt;
+  if (!(dtd > 0.0)) return;  // run finished: keep the state (no block reaches the epilogue)
+  const T dt = T(dtd);
+  const T dt_idx = T(dtd * geo.idx), dt_idy = T(dtd * geo.idy);
+  const int ntx = (geo.nx + TX - 1) / TX, nty = (geo.ny + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  unsigned int* ticket = tsync;
+  unsigned int* flag = tsync + 1;
+  volatile unsigned int* vstatus = &ctl->status;
+
+  for (;;) {
+    __syncthreads();  // the previous task is done with shared memory
+    if (threadIdx.x == 0) {
+      int tk = -1;
+      if ((*vstatus & kStatusTimeout) == 0u) {
+        const unsigned int q = atomicAdd(ticket, 1u);
+        if (q < (unsigned int)ntasks) tk = tasks[q];
+      }
+      task_s = tk;
+    }
+    __syncthreads();
+    const int task = task_s;
+    if (task < 0) break;
+    if (task < ntiles) {
+      // ---- final RK stage of tile `task` -> W ----
+      const int x0 = (task % ntx) * TX, y0 = (task / ntx) * TY;
+      load_tile_l2<T, NP, TX, TY, NT>(tile, Win, geo, x0, y0);
+      __syncthreads();
+      const U0FromL2<T> u0src{U0};
+      stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, W, geo, ph, 3, dt, x0, y0, u0src, &ctl->ntrace);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) st_release_gpu(&flag[task], 1u);
+    } else {
+      // ---- OE of tile `task - ntiles` from W -> Uout ----
+      const int t = task - ntiles;
+      const int tx_ = t % ntx, ty_ = t / ntx;
+      const int x0 = tx_ * TX, y0 = ty_ * TY;
+      if (threadIdx.x == 0) {
+        int cx[5], cy[5];
+        const int mx = halo_tiles(tx_, TX, geo.nx, geo.bc[0], geo.bc[1], cx);
+        const int my = halo_tiles(ty_, TY, geo.ny, geo.bc[2], geo.bc[3], cy);
+        bool ok = true;
+        const unsigned long long t0 = global_ns();
+        for (int b = 0; b < my && ok; ++b)
+          for (int a = 0; a < mx && ok; ++a) {
+            const unsigned int* f = &flag[cy[b] * ntx + cx[a]];
+            while (ld_acquire_gpu(f) == 0u) {
+              if ((*vstatus & kStatusTimeout) != 0u) {  // another block gave up first
+                ok = false;
+                break;
+              }
+              if (global_ns() - t0 > kWaitLimitNs) {
+                ok = false;
+                note_wait(ctl, kWaitTileFlag, (unsigned int)t, (unsigned int)(cy[b] * ntx + cx[a]), 0u);
+                break;
+              }
+              __nanosleep(100);
+            }
+          }
+        if (!ok) atomicOr(&ctl->status, kStatusTimeout);
+        ok_s = ok;
+      }
+      __syncthreads();
+      if (!ok_s) break;
+      load_tile_l2<T, NP, TX, TY, NT>(tile, W, geo, x0, y0);
+      __syncthreads();
+      T msx, msy;
+      oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, dt_idx, dt_idy, x0, y0, ctl,
+                                  &ctl->status, msx, msy);
+      const T mx = block_max<NT>(msx, red);
+      const T my = block_max<NT>(msy, red + 32);
+      if (threadIdx.x == 0) {
+        atomic_max_nonneg(&ctl->alpha_bits[0], (double)mx);
+        atomic_max_nonneg(&ctl->alpha_bits[1], (double)my);
+      }
+    }
+  }
+  if (threadIdx.x == 0) step_epilogue(ctl, gridDim.x, true);
 }
 
 // Max Rusanov speeds at cell averages -> ctl->dt (no time advance).

@@ -193,12 +193,15 @@ class Solver:
         self._check(lib().fam_sync(self._h))
 
     def tune(self, cfl: float, probe_steps: int = 2, cache_path: str | None = None) -> int:
-        """Pick the fastest 2D tile shape on the current state; returns its
-        index into TILES_2D (the state and clock are restored)."""
+        """Pick the fastest 2D tile shape, with the final stage and OE split or
+        fused, on the current state; returns the tile's index into TILES_2D
+        and leaves the split / fused choice in ``self.fused_oe`` (the state and
+        clock are restored)."""
         c = ctypes.c_int()
         self._check(lib().fam_tune(self._h, float(cfl), int(probe_steps),
                                    cache_path.encode() if cache_path else None, ctypes.byref(c)))
-        return c.value
+        self.fused_oe = c.value // 3
+        return c.value % 3
 
     def run_fixed(self, dts):
         d = np.ascontiguousarray(dts, dtype=np.float64)
