@@ -345,19 +345,21 @@ def batched_printed_ranges(a, nx, ks):
             "cell_stages": int(3 * np.sum(np.asarray(nx) * steps)), "seconds": sec}
 
 
-def batched2d_report(a, torch):
+def batched2d_report(a, torch, prec: int = 64):
     """Many independent 2D Euler problems (1024 instances, nx, ny log-uniform
     in [16, 256] -- 256 to 65536 cells, the cell-count spread of the 1D batch
     -- k in {3..6}, periodic density waves) advanced 50 steps in one
     persistent launch, against the plain per-instance step loop."""
     from paper_2609_26194_b300 import fam, inputs
     insts = inputs.batched_2d(1024, seed=6, nmin=16, nmax=256)
+    if prec == 32:
+        insts = [(k, U.astype(np.float32)) for k, U in insts]
     nx = [U.shape[-1] for _, U in insts]
     ny = [U.shape[-2] for _, U in insts]
     ks = [k for k, _ in insts]
     cells = sum(x * y for x, y in zip(nx, ny))
     cfl, nsteps = 0.4, a.batched2d_steps
-    b = fam.Batch(nx, ks, ny=ny, bc=fam.PERIODIC)
+    b = fam.Batch(nx, ks, ny=ny, bc=fam.PERIODIC, precision=prec)
     b.set_state([U for _, U in insts])
     tx, bps = b.tune(cfl, probe_steps=2)
     b.set_state([U for _, U in insts])
@@ -378,7 +380,7 @@ def batched2d_report(a, torch):
     plain_steps = 5
     solvers = []
     for (k, U), n, m in zip(insts, nx, ny):
-        sv = fam.Solver(2, n, m, k=k, equation=fam.EULER, bc=fam.PERIODIC,
+        sv = fam.Solver(2, n, m, k=k, equation=fam.EULER, bc=fam.PERIODIC, precision=prec,
                         tile2d=fam.TILES_2D.index((info["tile_x"], info["tile_y"])))
         sv.set_state(U)
         sv.step(cfl)
@@ -396,15 +398,16 @@ def batched2d_report(a, torch):
         sv.close()
     bv = 3.0 * cells * nsteps / batched_s
     pv = 3.0 * cells * plain_steps / plain_s
+    bpc = 256.0 if prec == 64 else 128.0  # algorithmic bytes per cell-stage
     return {"workload": "1024 x 2D Euler, nx, ny log-uniform [16,256], k in {3,4,5,6}, periodic, CFL 0.4, "
-                        "density waves (exact moments), FP64", "instances": len(nx), "cells": cells,
+                        f"density waves (exact moments), FP{prec}", "instances": len(nx), "cells": cells,
             "steps": nsteps, "value": bv, "unit": UNIT, "seconds": batched_s,
             "launch": {"tile": [info["tile_x"], info["tile_y"]], "grid_blocks": info["grid"],
                        "tiles": info["tiles"], "blocks_per_sm": bps, "kernel_launches": 1},
             "plain_loop": {"value": pv, "unit": UNIT, "steps": plain_steps, "seconds": plain_s,
                            "kernel_launches": 4 * len(nx) * plain_steps},
-            "hbm_roofline": {"algorithmic_bytes_per_cell_stage": 256.0, "achieved_gbs": 256.0 * bv / 1e9,
-                             "peak_gbs": _hbm_peak(), "frac": 256.0 * bv / 1e9 / _hbm_peak()},
+            "hbm_roofline": {"algorithmic_bytes_per_cell_stage": bpc, "achieved_gbs": bpc * bv / 1e9,
+                             "peak_gbs": _hbm_peak(), "frac": bpc * bv / 1e9 / _hbm_peak()},
             "speedup_vs_plain": bv / pv, "all_instances_advanced": bool(np.all(steps == nsteps)),
             "status": status}
 
@@ -696,6 +699,7 @@ def run_fam(a):
     if rank == 0 and world == 1 and not a.no_batched:
         line["batched"] = batched_report(a, torch)
         line["batched2d"] = batched2d_report(a, torch)
+        line["batched2d_f32"] = batched2d_report(a, torch, 32)
     if rank == 0 and world == 1 and not a.no_adjoint:
         line["adjoint"] = adjoint_report(a, torch)
     if rank == 0 and world == 1 and not a.no_configs:

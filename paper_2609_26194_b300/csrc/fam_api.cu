@@ -870,6 +870,7 @@ fam_status fam_residual(fam_t h, const void* U, void* R, int on_device) {
 fam_status fam_oe(fam_t h, double dt, const void* U, void* Uout, int on_device) {
   if (!h) return FAM_E_INVAL;
   if (!(dt >= 0.0)) return fail(h, FAM_E_INVAL, "dt must be >= 0");
+  dt = dt + 0.0;  // -0 -> +0: the kernels tell an override (>= 0) by the sign bit
   if (fam_status b = check_bc(h)) return b;
   fam_status s = copy_in(h, U, on_device, 1);
   if (s) return s;

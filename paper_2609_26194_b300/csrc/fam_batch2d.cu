@@ -10,8 +10,8 @@
 // instance's own maximum Rusanov speeds) after each step.  The per-tile
 // arithmetic is the single-problem device code (stage2d_tile, oe2d_tile),
 // so an instance evolves bit for bit as the single-problem kernels with the
-// same tile shape evolve it.  Tiles are staged with plain coalesced loads
-// (the instances' tensor maps would differ per tile).
+// same tile shape evolve it.  Tiles are staged with 16-byte vector loads
+// (load_tile_vec; the instances' tensor maps would differ per tile).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,21 +34,8 @@ typedef double Real;
 typedef float Real;
 #endif
 
-// Tile + 2-cell halo of all planes, padded coordinates (x0, y0) .. (x0 + HX,
-// y0 + HY), zero outside the padded arrays (the same box as the TMA load of
-// the single-problem kernels).
-template <typename T, int NP, int HX, int HY, int NT>
-__device__ __forceinline__ void load_tile2d_plain(T* tile, const T* __restrict__ in, const BatchInst& I, int x0,
-                                                  int y0) {
-  for (int q = threadIdx.x; q < NP * HY * HX; q += NT) {
-    const int p = q / (HY * HX), r = q - p * (HY * HX);
-    const int y = y0 + r / HX, x = x0 + r % HX;
-    tile[q] = (x < I.px && y < I.rows) ? in[I.off + (long long)p * I.plane + (long long)y * I.px + x] : T(0);
-  }
-}
-
 template <typename T, class PH, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 1)
+__global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
     batched2d_run(const BatchInst* __restrict__ inst, const Geo* __restrict__ geos, const int4* __restrict__ tiles,
                   int ntiles, int ninst, T* A, T* B, T* C, BatchCtl* ictl, BatchGlobal* g, const PH ph, int nsteps,
                   double cfl, int oe_type, int bc, int init) {
@@ -123,17 +110,17 @@ __global__ void __launch_bounds__(TX * TY, 1)
         // the instance's geometry stays in (cached) global memory rather than in registers
         const Geo& geo = geos[td.x];
         __syncthreads();
-        load_tile2d_plain<T, NP, HX, HY, NT>(tile, in, I, td.y, td.z);
+        load_tile_vec<T, NP, TX, TY, NT>(tile, in + I.off, geo, td.y, td.z);
         __syncthreads();
         T* Uo = out + I.off;
         if (pass < 4) {
           const U0FromGlobal<T> u0src{A + I.off};
           const T dt = T(dtd);
           switch (I.k) {
-            case 3: stage2d_tile<T, 3, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
-            case 4: stage2d_tile<T, 4, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
-            case 5: stage2d_tile<T, 5, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
-            default: stage2d_tile<T, 6, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace); break;
+            case 3: stage2d_tile<T, 3, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace, T(geo.idx), T(geo.idy)); break;
+            case 4: stage2d_tile<T, 4, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace, T(geo.idx), T(geo.idy)); break;
+            case 5: stage2d_tile<T, 5, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace, T(geo.idx), T(geo.idy)); break;
+            default: stage2d_tile<T, 6, PH, TX, TY>(tile, xL, xR, yB, yT, Uo, geo, ph, pass, dt, td.y, td.z, u0src, &ictl[td.x].ntrace, T(geo.idx), T(geo.idy)); break;
           }
         } else {
           const T dt_idx = T(dtd * I.idx), dt_idy = T(dtd * I.idy);

@@ -250,6 +250,11 @@ __device__ __forceinline__ bool less_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);
 }
 __device__ __forceinline__ bool less_nonneg(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+// x > 0 and x >= 0 for the step sizes (finite or +0 by construction: the
+// epilogue stores 0 for a non-finite step), on the bit pattern: integer
+// compares, so that the FP32 kernels keep the slow FP64 pipe free.
+__device__ __forceinline__ bool pos_bits(double x) { return __double_as_longlong(x) > 0ll; }
+__device__ __forceinline__ bool nonneg_bits(double x) { return __double_as_longlong(x) >= 0ll; }
 // isnan on the bit pattern (integer compare)
 __device__ __forceinline__ bool nan_bits(double v) {
   return (__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll;
@@ -319,11 +324,25 @@ template <> struct Fast<double> {
   static __device__ __forceinline__ double exp_(double x) { return exp(x); }
 };
 
+// FP32: the hardware approximations, one MUFU instruction each (1/x within
+// 1 ulp, sqrt within 2^-23 relative), in place of the correctly rounded
+// multi-instruction sequences; the FP32 stage kernel is issue bound, and its
+// error against the FP64 oracle is dominated by the accumulated rounding of
+// the stage arithmetic.  exp(x) = 2^(x log2 e), with the product rounded
+// once (relative error about |x| 2^-24 more, for the OE's damping factor).
 template <> struct Fast<float> {
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-  static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+  static __device__ __forceinline__ float rcp(float x) { return rcp_approx_f32(x); }
+  static __device__ __forceinline__ float rsqrt(float x) { return rsqrt_approx_f32(x); }
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  static __device__ __forceinline__ float exp_(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * 1.4426950408889634f));
+    return r;
+  }
 };
 
 // ---------------------------------------------------------------------------

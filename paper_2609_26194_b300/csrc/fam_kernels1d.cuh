@@ -119,8 +119,8 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
   for (int c = 0; c < NC; ++c) avg[c] = tile[(size_t)(c * 2) * HX + hx];
   T V1[NC];
   ph.vol_finish(VA, avg, V1);
-  double w0, w1;
-  stage_weights(stage, w0, w1);
+  T w0, w1;
+  stage_weights<T>(stage, w0, w1);
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const T fl = fL[tx * NC + c], fr = fL[(tx + 1) * NC + c];
@@ -139,7 +139,7 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
           v = us + dt * R[m];
         } else {
           const T u0 = U0[cell_index(geo, p, 0, i)];
-          v = T(w0) * u0 + T(w1) * (us + dt * R[m]);
+          v = w0 * u0 + w1 * (us + dt * R[m]);
         }
       }
       store_with_ghosts(Uout, geo, p, 0, i, v);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(TX)
   uint64_t* bar = reinterpret_cast<uint64_t*>(fR + (TX + 1) * NC);
 
   const double dtd = (stage == 0) ? 0.0 : ctl->dt;
-  if (stage != 0 && !(dtd > 0.0)) return;
+  if (stage != 0 && !pos_bits(dtd)) return;
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;
@@ -255,9 +255,9 @@ __global__ void __launch_bounds__(TX)
   uint64_t* bar = reinterpret_cast<uint64_t*>(sp + RX);
   double* red = reinterpret_cast<double*>(bar + 2);
 
-  const double dtd = dt_override >= 0.0 ? dt_override : ctl->dt;
-  const bool reduce = dt_override < 0.0;
-  if (!(dtd > 0.0) && reduce) return;
+  const bool reduce = !nonneg_bits(dt_override);
+  const double dtd = reduce ? ctl->dt : dt_override;
+  if (!pos_bits(dtd) && reduce) return;
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;

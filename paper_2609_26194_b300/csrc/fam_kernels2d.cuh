@@ -24,11 +24,13 @@ struct Coefs2D {
   T a0, a1, a2;  // Shu--Osher: out = a1 * U0 + a2 * (Us + dt R)   (a0 unused)
 };
 
-__device__ __forceinline__ void stage_weights(int stage, double& w0, double& w1) {
-  // out = w0 * U0 + w1 * (Us + dt R)
-  if (stage == 1) { w0 = 0.0; w1 = 1.0; }
-  else if (stage == 2) { w0 = 0.75; w1 = 0.25; }
-  else { w0 = 1.0 / 3.0; w1 = 2.0 / 3.0; }
+// Shu--Osher weights of eq. 12, out = w0 * U0 + w1 * (Us + dt R), as
+// constants of the kernel's type (no FP64 conversion in the FP32 kernels).
+template <typename T>
+__device__ __forceinline__ void stage_weights(int stage, T& w0, T& w1) {
+  if (stage == 1) { w0 = T(0.0); w1 = T(1.0); }
+  else if (stage == 2) { w0 = T(0.75); w1 = T(0.25); }
+  else { w0 = T(1.0 / 3.0); w1 = T(2.0 / 3.0); }
 }
 
 // Padded positions (and signs) at which interior index i of one direction
@@ -186,7 +188,7 @@ template <typename T, int K, class PH, int TX, int TY, class U0Src>
 __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, T* xR, T* yB, T* yT,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const int stage,
                                              const T dt, const int x0, const int y0, const U0Src& u0src,
-                                             unsigned long long* ntrace) {
+                                             unsigned long long* ntrace, const T idx_, const T idy_) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int HX = S::HX, HY = S::HY;
@@ -380,14 +382,13 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   const int i = x0 + tx, j = y0 + ty;
   if (!u0src.ready()) return;
   if (i >= geo.nx || j >= geo.ny) return;
-  const T idx_ = T(geo.idx), idy_ = T(geo.idy);
   T avg[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) avg[c] = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
   T V1[NC], V2[NC];
   ph.vol_finish(VA, avg, V1, V2);
-  double w0, w1;
-  stage_weights(stage, w0, w1);
+  T w0, w1;
+  stage_weights<T>(stage, w0, w1);
   // half weights (the face slots hold twice the flux) and half weight x node
   T hw[4], hwx[4];
 #pragma unroll
@@ -428,7 +429,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
           v = us + dt * R[m];
         } else {
           const T u0 = u0src.u0(geo, p, j, i, ty, hx);
-          v = T(w0) * u0 + T(w1) * (us + dt * R[m]);
+          v = w0 * u0 + w1 * (us + dt * R[m]);
         }
       }
       store_with_ghosts(Uout, geo, p, j, i, v);
@@ -463,9 +464,16 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   T* yT = yB + S::YF;
   uint64_t* bar = reinterpret_cast<uint64_t*>(yT + S::YF);  // [0] tile, [1] U^n
 
+  // launch constants in T, converted once per block (in the FP32 kernels a
+  // conversion from FP64 occupies the slow FP64 pipe)
+  __shared__ T cst[3];
   const double dtd = (stage == 0) ? 0.0 : ctl->dt;
-  if (stage != 0 && !(dtd > 0.0)) return;  // run finished: keep the state
-  const T dt = T(dtd);
+  if (stage != 0 && !pos_bits(dtd)) return;  // run finished: keep the state
+  if (threadIdx.x == 0) {
+    cst[0] = T(dtd);
+    cst[1] = T(geo.idx);
+    cst[2] = T(geo.idy);
+  }
 
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const bool want_u0 = stage >= 2;
@@ -485,7 +493,9 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   }
 
   const U0FromSmem<T, TX, TY> u0src{u0s, bar + 1, ctl, want_u0};
-  stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, dt, x0, y0, u0src, &ctl->ntrace);
+  // (load_tile's barrier has made cst visible)
+  stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, cst[0], x0, y0, u0src, &ctl->ntrace,
+                                 cst[1], cst[2]);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,8 +658,15 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
   }
 }
 
+// Resident CTAs per SM of the OE kernel: FP32 keeps its registers at 80 so
+// that 6 CTAs of 128 threads fit.
+template <typename T, int NT>
+constexpr int oe_min_blocks() {
+  return sizeof(T) == 8 ? 1 : (768 / NT);
+}
+
 template <typename T, int K, class PH, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 1)
+__global__ void __launch_bounds__(TX * TY, oe_min_blocks<T, TX * TY>())
     oe2d(const __grid_constant__ CUtensorMap tm_in, T* __restrict__ Uout, const Geo geo, const PH ph,
          FamCtl* __restrict__ ctl, const int oe_type, const T gamma_k, const int q6, const double dt_override) {
   constexpr int NC = PH::NC;
@@ -665,17 +682,21 @@ __global__ void __launch_bounds__(TX * TY, 1)
   uint64_t* bar = reinterpret_cast<uint64_t*>(sp + 2 * RX * RY);
   double* red = reinterpret_cast<double*>(bar + 2);
 
-  const double dtd = dt_override >= 0.0 ? dt_override : ctl->dt;
-  const bool reduce = dt_override < 0.0;
-  if (!(dtd > 0.0) && reduce) return;
-  const T dt_idx = T(dtd * geo.idx), dt_idy = T(dtd * geo.idy);
+  const bool reduce = !nonneg_bits(dt_override);
+  const double dtd = reduce ? ctl->dt : dt_override;
+  if (!pos_bits(dtd) && reduce) return;
+  __shared__ T cst[2];  // dt/dx, dt/dy in T, once per block
+  if (threadIdx.x == 0) {
+    cst[0] = T(dtd * geo.idx);
+    cst[1] = T(dtd * geo.idy);
+  }
 
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile<T, NP, HX, HY>(tile, bar, &tm_in, x0, y0, ctl)) return;
 
   T my_speed_x, my_speed_y;
-  oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, dt_idx, dt_idy, x0, y0, ctl,
+  oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, cst[0], cst[1], x0, y0, ctl,
                               &ctl->status, my_speed_x, my_speed_y);
   if (!reduce) return;
   const T mx = block_max<NT>(my_speed_x, red);
@@ -740,9 +761,11 @@ __host__ __device__ inline int halo_tiles(int t, int TW, int n, int lo, int hi, 
 }
 
 // Load the tile + halo box ((TX+4) x (TY+4) x NP at padded (x0, y0)) of W
-// with L2-only vector loads (W was written by other blocks of this launch, so
-// no line of it may come from this SM's L1); outside the padded planes: 0.
-template <typename T, int NP, int TX, int TY, int NT>
+// with 16-byte vector loads; outside the padded planes: 0.  L2ONLY: through
+// L2 only (W was written by other blocks of the same launch, so no line of it
+// may come from this SM's L1).  Needs 16-byte aligned rows (padded pitch a
+// multiple of 4 elements, x0 a multiple of 4 / 2 elements in FP32 / FP64).
+template <typename T, int NP, int TX, int TY, int NT, bool L2ONLY = true>
 __device__ __forceinline__ void load_tile_l2(T* tile, const T* __restrict__ W, const Geo& g, int x0, int y0) {
   constexpr int HX = TX + 4, HY = TY + 4;
   constexpr int VW = 16 / (int)sizeof(T);  // elements per 16-byte vector
@@ -756,11 +779,13 @@ __device__ __forceinline__ void load_tile_l2(T* tile, const T* __restrict__ W, c
     if (y < g.rows && xv < g.px) {
       const T* src = W + (long long)p * g.plane + (long long)y * g.px + xv;
       if constexpr (sizeof(T) == 8) {
-        const double2 v = __ldcg(reinterpret_cast<const double2*>(src));
+        const double2* s2 = reinterpret_cast<const double2*>(src);
+        const double2 v = L2ONLY ? __ldcg(s2) : __ldg(s2);
         dst[0] = v.x;
         dst[1] = v.y;
       } else {
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        const float4 v = L2ONLY ? __ldcg(s4) : __ldg(s4);
         dst[0] = v.x;
         dst[1] = v.y;
         dst[2] = v.z;
@@ -771,6 +796,12 @@ __device__ __forceinline__ void load_tile_l2(T* tile, const T* __restrict__ W, c
       for (int e = 0; e < VW; ++e) dst[e] = T(0);
     }
   }
+}
+
+// The same through L1 (read-only data of the launch: the batch's stage input).
+template <typename T, int NP, int TX, int TY, int NT>
+__device__ __forceinline__ void load_tile_vec(T* tile, const T* __restrict__ W, const Geo& g, int x0, int y0) {
+  load_tile_l2<T, NP, TX, TY, NT, false>(tile, W, g, x0, y0);
 }
 
 template <typename T, int NC, int TX, int TY>
@@ -805,9 +836,15 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   __shared__ int task_s, ok_s;
 
   const double dtd = ctl->dt;
-  if (!(dtd > 0.0)) return;  // run finished: keep the state (no block reaches the epilogue)
-  const T dt = T(dtd);
-  const T dt_idx = T(dtd * geo.idx), dt_idy = T(dtd * geo.idy);
+  if (!pos_bits(dtd)) return;  // run finished: keep the state (no block reaches the epilogue)
+  __shared__ T cst[5];  // dt, 1/dx, 1/dy, dt/dx, dt/dy in T, once per block
+  if (threadIdx.x == 0) {
+    cst[0] = T(dtd);
+    cst[1] = T(geo.idx);
+    cst[2] = T(geo.idy);
+    cst[3] = T(dtd * geo.idx);
+    cst[4] = T(dtd * geo.idy);
+  }
   const int ntx = (geo.nx + TX - 1) / TX, nty = (geo.ny + TY - 1) / TY;
   const int ntiles = ntx * nty;
   unsigned int* ticket = tsync;
@@ -833,7 +870,8 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
       load_tile_l2<T, NP, TX, TY, NT>(tile, Win, geo, x0, y0);
       __syncthreads();
       const U0FromL2<T> u0src{U0};
-      stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, W, geo, ph, 3, dt, x0, y0, u0src, &ctl->ntrace);
+      stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, W, geo, ph, 3, cst[0], x0, y0, u0src, &ctl->ntrace,
+                                     cst[1], cst[2]);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) st_release_gpu(&flag[task], 1u);
@@ -872,7 +910,7 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
       load_tile_l2<T, NP, TX, TY, NT>(tile, W, geo, x0, y0);
       __syncthreads();
       T msx, msy;
-      oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, dt_idx, dt_idy, x0, y0, ctl,
+      oe2d_tile<T, K, PH, TX, TY>(tile, fc, sp, Uout, geo, ph, oe_type, gamma_k, q6, cst[3], cst[4], x0, y0, ctl,
                                   &ctl->status, msx, msy);
       const T mx = block_max<NT>(msx, red);
       const T my = block_max<NT>(msy, red + 32);
