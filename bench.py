@@ -336,13 +336,41 @@ def batched_printed_ranges(a, nx, ks):
     _, _, steps = b.times()
     b.close()
     stopped = bad > 0
-    return {"rho": [0.1, 2.0], "umax": 1.0, "p": [0.1, 10.0], "steps": a.batched_steps, "status": status,
-            "completed": int(np.sum(~stopped)), "stopped": int(np.sum(stopped)),
-            "stop_step_quartiles": ([int(v) for v in np.percentile(bad[stopped], [0, 25, 50, 75, 100])]
-                                    if stopped.any() else []),
-            "nonphysical_traces": int(np.sum(ntr)),
-            "instances_with_nonphysical_traces": int(np.sum(ntr > 0)),
-            "cell_stages": int(3 * np.sum(np.asarray(nx) * steps)), "seconds": sec}
+    out = {"rho": [0.1, 2.0], "umax": 1.0, "p": [0.1, 10.0], "steps": a.batched_steps, "status": status,
+           "completed": int(np.sum(~stopped)), "stopped": int(np.sum(stopped)),
+           "stop_step_quartiles": ([int(v) for v in np.percentile(bad[stopped], [0, 25, 50, 75, 100])]
+                                   if stopped.any() else []),
+           "nonphysical_traces": int(np.sum(ntr)),
+           "instances_with_nonphysical_traces": int(np.sum(ntr > 0)),
+           "cell_stages": int(3 * np.sum(np.asarray(nx) * steps)), "seconds": sec}
+    # the same batch with the BP/PP safeguard, at the same CFL and at the
+    # bound of its guarantee (1/12 for k = 5, 6)
+    for cfl in (0.3, 1.0 / 12.0):
+        b = fam.Batch(nx, ks, bc=fam.OUTFLOW)
+        b.set_option("pp_limiter", 1)
+        b.set_state(states)
+        torch_sync()
+        t0 = time.perf_counter()
+        b.run(a.batched_steps, cfl)
+        try:
+            b.sync()
+            status = "ok"
+        except fam.FamError as e:
+            status = str(e)
+        sec = time.perf_counter() - t0
+        ntr, _, bad = b.health()
+        _, _, steps = b.times()
+        b.close()
+        cs = 3.0 * float(np.sum(np.asarray(nx) * steps))
+        out[f"safeguard_cfl_{cfl:.4g}"] = {"status": status, "completed": int(np.sum(bad == 0)),
+                                           "stopped": int(np.sum(bad > 0)), "nonphysical_traces": int(np.sum(ntr)),
+                                           "value": cs / sec, "unit": UNIT, "seconds": sec}
+    return out
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
 
 
 def batched2d_report(a, torch, prec: int = 64):
@@ -495,6 +523,18 @@ def configs_report(a, torch):
     out["euler2d_smooth_4096_k5_f32"] = {"value": 3.0 * n * n * steps / sec, "seconds": sec, "steps": steps,
                                          "tile": list(tile)}
     s.close()
+    # the bench workload (FP64, k = 5) with the BP/PP safeguard on: what the
+    # per-stage scaling-factor kernel costs where it changes nothing
+    st = torch.cuda.Stream()
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC, precision=64, pp_limiter=1,
+                   stream=st.cuda_stream)
+    s.set_state(data["smooth"])
+    s.run_steps(steps, 0.55)
+    s.set_state(data["smooth"])
+    sec = timed(s, st, lambda: s.run_steps(steps, 0.55))
+    out["euler2d_smooth_4096_k5_f64_safeguard"] = {"value": 3.0 * n * n * steps / sec, "seconds": sec,
+                                                   "steps": steps}
+    s.close()
     return {"unit": UNIT, "note": "each run: CUDA events around one graph-captured multi-step launch "
                                   "(after an untimed run of the same length)", "runs": out,
             "rectangles_printed_ranges": printed_rectangles_report(torch)}
@@ -523,6 +563,38 @@ def printed_rectangles_report(torch, n: int = 4096, max_steps: int = 20):
                 break
         out[f"k{k}_f64"] = {"status": status, "steps": done, "nonphysical_traces": s.nonphysical_traces(),
                             "face_points_per_step": 3 * 2 * n * (n + 1) * 4}
+        s.close()
+    # the same data with the BP/PP safeguard (option pp_limiter) at the same
+    # CFL: timed with CUDA events around one graph-captured run of max_steps
+    for k, prec in ((4, 64), (6, 64), (5, 32)):
+        cfl = 0.4 if k == 4 else 0.55
+        Up = U.astype(np.float64 if prec == 64 else np.float32)
+        st = torch.cuda.Stream()
+        s = fam.Solver(2, n, n, k=k, equation=fam.EULER, bc=fam.PERIODIC, precision=prec, pp_limiter=1,
+                       stream=st.cuda_stream)
+        s.set_state(Up)
+        s.run_steps(max_steps, cfl)  # builds the graph
+        try:
+            s.sync()
+        except fam.FamError:
+            pass
+        s.set_state(Up)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.run_steps(max_steps, cfl)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        try:
+            s.sync()
+            status = "completed"
+        except fam.FamError as e:
+            status = str(e)
+        t, _, nst = s.time()
+        out[f"k{k}_f{prec}_safeguard"] = {"status": status, "steps": nst, "t": t,
+                                           "nonphysical_traces": s.nonphysical_traces(),
+                                           "value": 3.0 * n * n * max_steps / sec, "unit": UNIT, "seconds": sec}
         s.close()
     return out
 

@@ -87,6 +87,19 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
  *   "dt_max"     upper bound on the step size (<= 0: none)
  *   "tile2d"     2D tile shape of the stage / OE kernels: 0 = 32 x 8 (default),
  *                1 = 32 x 4, 2 = 16 x 8 cells (see fam_tune)
+ *   "pp_limiter" Euler only: 1 turns on the BP/PP safeguard the paper
+ *                applies after RK substeps in some tests (Sec. 2.3 remarks,
+ *                Alg. 1; it cites its construction without defining it).
+ *                Built as the Zhang-Shu scaling of every stage's
+ *                reconstruction towards the cell average, so that density
+ *                and pressure are admissible at the points of a
+ *                Gauss-Lobatto decomposition of the average (3 points for
+ *                k <= 4, 4 for k = 5, 6) and at the volume Gauss points; the
+ *                CFL rule then takes its speeds at those points, and a
+ *                forward-Euler step keeps the averages admissible for CFL
+ *                numbers up to 1/6 (k <= 4) or 1/12 (k = 5, 6).  The final
+ *                stage and the OE then run split; no adjoint.  0 (default):
+ *                off, the scheme of the paper's tests without BP/PP
  *   "fused_oe"   2D only: 1 runs the final RK stage and the OE in one
  *                persistent launch (not in the paper: tiles of the final
  *                stage and, once the tiles around them are done, the OE of
@@ -243,7 +256,8 @@ fam_status fam_batch2d_create(fam_batch_t* out, int n_inst, const int* nx, const
 /* Keys: "oe_type" (0 / 2), "gamma_k" (<= 0: defaults per order), "ax",
  * "tile_x" (1D: 64 / 128 / 256 cells per tile), "tile2d" (2D: 0 / 1 / 2 for
  * 32x8 / 32x4 / 16x8 cells per tile), "blocks_per_sm" (<= 0: the occupancy
- * maximum), "wait_limit_ns" (how long a block waits at the persistent
+ * maximum), "pp_limiter" (1D Euler: the BP/PP safeguard of fam_set_option,
+ * in every instance), "wait_limit_ns" (how long a block waits at the persistent
  * kernel's grid barrier before the launch gives up with FAM_E_TIMEOUT from
  * fam_batch_sync; 0 restores the default of 2 s; at most 60 s),
  * "test_barrier_extra" (test hook, 0 or 1: the grid barrier waits for one

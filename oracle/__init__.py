@@ -49,7 +49,7 @@ class _Problem(ctypes.Structure):
         ("inflow", (ctypes.c_double * 4) * 4),
         ("gamma", ctypes.c_double), ("ax", ctypes.c_double), ("ay", ctypes.c_double),
         ("oe_type", ctypes.c_int), ("gamma_k", ctypes.c_double), ("oe_jump_q6", ctypes.c_int),
-        ("oe_mean", ctypes.c_int),
+        ("oe_mean", ctypes.c_int), ("pp_limiter", ctypes.c_int),
     ]
 
 
@@ -74,6 +74,7 @@ class Problem:
     gamma_k: float = 0.0
     oe_jump_q6: int = 1
     oe_mean: int = 0
+    pp_limiter: int = 0
 
     @property
     def ncomp(self) -> int:
@@ -101,6 +102,7 @@ class Problem:
         p.gamma, p.ax, p.ay = self.gamma, self.ax, self.ay
         p.oe_type, p.gamma_k, p.oe_jump_q6 = self.oe_type, self.gamma_k, self.oe_jump_q6
         p.oe_mean = self.oe_mean
+        p.pp_limiter = self.pp_limiter
         return p
 
 

@@ -375,6 +375,163 @@ static int cell_coeffs(const or_problem* P, padded* A, int c, int j, int i, doub
 /* Residual                                                             */
 /* ------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------ */
+/* Optional BP/PP safeguard (Sec. 2.3 remarks, Alg. 1; the paper cites its */
+/* limiter, CDW1/CDW2, without defining it): the Zhang-Shu scaling of a    */
+/* cell's reconstruction towards its average, p~ = u_bar + theta (p -     */
+/* u_bar), so that every point of a cell-average decomposition and every  */
+/* volume Gauss point holds an admissible Euler state.                    */
+/* ------------------------------------------------------------------ */
+
+/* Gauss-Lobatto nodes on [-1/2,1/2] whose rule is exact on P_{k-1}: 3 points
+ * for k <= 4, 4 points for k = 5, 6. */
+static int lobatto_nodes(int k, double* x) {
+  if (k <= 4) {
+    x[0] = -0.5; x[1] = 0.0; x[2] = 0.5;
+    return 3;
+  }
+  x[0] = -0.5; x[1] = -0.5 / sqrt(5.0); x[2] = 0.5 / sqrt(5.0); x[3] = 0.5;
+  return 4;
+}
+
+/* Points of the check: 1D the Lobatto nodes and the 4 Gauss nodes; 2D the
+ * Lobatto x Gauss, Gauss x Lobatto and Gauss x Gauss products.  Returns the
+ * number of points (at most 48). */
+static int pp_points(int d, int k, double* xi, double* eta) {
+  double gl[4], g[4], w[4];
+  int nl = lobatto_nodes(k, gl);
+  or_gauss4(g, w);
+  int n = 0;
+  if (d == 1) {
+    for (int a = 0; a < nl; ++a) { xi[n] = gl[a]; eta[n++] = 0.0; }
+    for (int a = 0; a < 4; ++a) { xi[n] = g[a]; eta[n++] = 0.0; }
+    return n;
+  }
+  for (int a = 0; a < nl; ++a)
+    for (int b = 0; b < 4; ++b) { xi[n] = gl[a]; eta[n++] = g[b]; }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < nl; ++b) { xi[n] = g[a]; eta[n++] = gl[b]; }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) { xi[n] = g[a]; eta[n++] = g[b]; }
+  return n;
+}
+
+static double pressure(double gm1, int d, const double* u) {
+  double m2 = u[1] * u[1] + (d == 2 ? u[2] * u[2] : 0.0);
+  return gm1 * (u[d + 1] - 0.5 * m2 / u[0]);
+}
+
+/* The t in [0, 1] with p(ub + t dw) = eps, given p(ub) > eps > p(ub + dw):
+ * the root in (0, 1) of rho(t) (E(t) - eps/(gamma-1)) - |m(t)|^2 / 2. */
+static double pressure_root(double gm1, int d, const double* ub, const double* dw, double eps) {
+  int e = d + 1;
+  double Eh = ub[e] - eps / gm1, dm2 = dw[1] * dw[1], mdm = ub[1] * dw[1], m2 = ub[1] * ub[1];
+  if (d == 2) { dm2 += dw[2] * dw[2]; mdm += ub[2] * dw[2]; m2 += ub[2] * ub[2]; }
+  double a = dw[e] * dw[0] - 0.5 * dm2;
+  double b = Eh * dw[0] + ub[0] * dw[e] - mdm;
+  double c = Eh * ub[0] - 0.5 * m2;
+  if (fabs(a) < 1e-14 * (fabs(b) + fabs(c))) return -c / b;
+  /* roots q / a and c / q with q = -(b + sign(b) sqrt(disc)) / 2: the same
+   * pair as (-b -+ sqrt(disc)) / 2a without the cancellation of -b + sqrt
+   * when b^2 >> |4ac| (the small root, the one wanted, would lose digits) */
+  double disc = sqrt(fmax(b * b - 4.0 * a * c, 0.0));
+  double q = -0.5 * (b + copysign(disc, b));
+  double r1 = q / a, r2 = c / q;
+  double t = 1.0;
+  if (r1 >= 0.0 && r1 <= 1.0) t = r1;
+  if (r2 >= 0.0 && r2 <= 1.0 && r2 < t) t = r2;
+  return t;
+}
+
+/* Scale the Euler reconstruction of one cell, given as nc coefficient arrays
+ * (coefficient 0 is the cell average; basis functions 1.. have zero mean):
+ * density first (theta1), then all components (theta2). */
+static void pp_limit_cell(const or_problem* P, int ncoef, double* const* cf, double* smax);
+
+/* Rusanov speeds (x, y) maxed over the check points of the limited
+ * reconstruction of every cell: the wave speeds of the CFL condition under
+ * which the scaled reconstruction keeps the averages admissible (Zhang-Shu). */
+static void pp_max_speed(const or_problem* P, const double* U, double* ax, double* ay) {
+  padded A;
+  double mx = 0.0, my = 0.0;
+  if (pad_state(P, U, &A)) { *ax = *ay = NAN; return; }
+  int nc = A.nc, ny = P->d == 1 ? 1 : P->ny;
+  int ncoef = P->d == 1 ? P->k : (P->k == 3 ? 6 : P->k == 4 ? 10 : P->k == 5 ? 15 : 21);
+#pragma omp parallel for reduction(max : mx, my)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < P->nx; ++i) {
+      double cbuf[4][23], *cf[4], sm[2];
+      for (int c = 0; c < nc; ++c) {
+        cf[c] = cbuf[c];
+        cell_coeffs(P, &A, c, j, i, cf[c]);
+      }
+      pp_limit_cell(P, ncoef, cf, sm);
+      if (sm[0] > mx) mx = sm[0];
+      if (sm[1] > my) my = sm[1];
+    }
+  free(A.v);
+  *ax = mx;
+  *ay = my;
+}
+
+static void pp_limit_cell(const or_problem* P, int ncoef, double* const* cf, double* smax) {
+  int d = P->d, nc = d + 2;
+  double gm1 = P->gamma - 1.0;
+  double xi[48], eta[48];
+  int np = pp_points(d, P->k, xi, eta);
+  double ub[4];
+  for (int c = 0; c < nc; ++c) ub[c] = cf[c][0];
+  double pb = ub[0] > 0.0 ? pressure(gm1, d, ub) : -1.0;
+  double t1 = 1.0, t2 = 1.0;
+  if (!(ub[0] > 0.0) || !(pb > 0.0)) {
+    t1 = t2 = 0.0;  /* the average itself is not admissible: keep it constant */
+  } else {
+    /* targets: density min(1e-13, rho_bar) (Zhang-Shu); pressure 1e-10 p_bar,
+     * relative to the cell, since the rounding of E - |m|^2 / (2 rho) at a
+     * point scaled to a small density is about 1e-14 of E and would turn an
+     * absolute 1e-13 negative */
+    double eps = fmin(1e-13, ub[0]), epsp = 1e-10 * pb;
+    double u[48][4];
+    double rmin = ub[0];
+    for (int q = 0; q < np; ++q) {
+      for (int c = 0; c < nc; ++c)
+        u[q][c] = d == 1 ? or_eval1d(ncoef, cf[c], xi[q]) : or_eval2d(ncoef, cf[c], xi[q], eta[q]);
+      if (u[q][0] < rmin) rmin = u[q][0];
+    }
+    if (rmin < eps) t1 = (ub[0] - eps) / (ub[0] - rmin);
+    for (int q = 0; q < np; ++q) {
+      double w[4], dw[4];
+      for (int c = 0; c < nc; ++c) w[c] = u[q][c];
+      w[0] = ub[0] + t1 * (u[q][0] - ub[0]);
+      if (pressure(gm1, d, w) < epsp) {
+        for (int c = 0; c < nc; ++c) dw[c] = w[c] - ub[c];
+        double t = pressure_root(gm1, d, ub, dw, epsp);
+        if (t < t2) t2 = t;
+      }
+    }
+  }
+  if (!(t1 == 1.0 && t2 == 1.0))
+    for (int l = 1; l < ncoef; ++l) {
+      cf[0][l] *= t1 * t2;
+      for (int c = 1; c < nc; ++c) cf[c][l] *= t2;
+    }
+  if (smax) {
+    smax[0] = phys_speed(P, 0, ub);
+    smax[1] = d == 2 ? phys_speed(P, 1, ub) : 0.0;
+    for (int q = 0; q < np; ++q) {
+      double u[4];
+      for (int c = 0; c < nc; ++c)
+        u[c] = d == 1 ? or_eval1d(ncoef, cf[c], xi[q]) : or_eval2d(ncoef, cf[c], xi[q], eta[q]);
+      double sx = phys_speed(P, 0, u);
+      if (sx > smax[0]) smax[0] = sx;
+      if (d == 2) {
+        double sy = phys_speed(P, 1, u);
+        if (sy > smax[1]) smax[1] = sy;
+      }
+    }
+  }
+}
+
 static int residual_1d(const or_problem* P, padded* A, double* R) {
   int nx = P->nx, nc = A->nc;
   double dx = (P->x1 - P->x0) / nx;
@@ -386,8 +543,14 @@ static int residual_1d(const or_problem* P, padded* A, double* R) {
   if (!C || !F) { free(C); free(F); return -1; }
   int ncoef = P->k;
 #pragma omp parallel for
-  for (int i = -1; i <= nx; ++i)
+  for (int i = -1; i <= nx; ++i) {
     for (int c = 0; c < nc; ++c) cell_coeffs(P, A, c, 0, i, &C[((size_t)(i + 1) * nc + c) * 6]);
+    if (P->pp_limiter && P->eq == OR_EULER) {
+      double* cf[4];
+      for (int c = 0; c < nc; ++c) cf[c] = &C[((size_t)(i + 1) * nc + c) * 6];
+      pp_limit_cell(P, ncoef, cf, NULL);
+    }
+  }
   /* face f sits between cells f-1 and f */
   long long bad = 0;
 #pragma omp parallel for reduction(+ : bad)
@@ -435,8 +598,14 @@ static int residual_2d(const or_problem* P, padded* A, double* R) {
 #define CC(j, i, c) (&C[(((size_t)((j) + 1) * (nx + 2) + ((i) + 1)) * nc + (c)) * 23])
 #pragma omp parallel for
   for (int j = -1; j <= ny; ++j)
-    for (int i = -1; i <= nx; ++i)
+    for (int i = -1; i <= nx; ++i) {
       for (int c = 0; c < nc; ++c) cell_coeffs(P, A, c, j, i, CC(j, i, c));
+      if (P->pp_limiter && P->eq == OR_EULER) {
+        double* cf[4];
+        for (int c = 0; c < nc; ++c) cf[c] = CC(j, i, c);
+        pp_limit_cell(P, ncoef, cf, NULL);
+      }
+    }
   long long bad = 0;
 #pragma omp parallel for reduction(+ : bad)
   for (int j = 0; j < ny; ++j)
@@ -538,7 +707,8 @@ void or_max_speed(const or_problem* P, const double* U, double* ax, double* ay) 
 
 double or_dt(const or_problem* P, const double* U, double cfl, int smooth) {
   double ax, ay;
-  or_max_speed(P, U, &ax, &ay);
+  if (P->pp_limiter && P->eq == OR_EULER) pp_max_speed(P, U, &ax, &ay);
+  else or_max_speed(P, U, &ax, &ay);
   double dx = (P->x1 - P->x0) / P->nx;
   double e = smooth ? P->k / 3.0 : 1.0;
   if (P->d == 1) return cfl * pow(dx, e) / ax;

@@ -44,6 +44,10 @@ typedef struct {
   int oe_jump_q6;     /* 2D k=6: 1 = jumps of full Q6 (printed matrices), 0 = of p6 */
   int oe_mean;        /* Type II: 0 = S_Lambda the unnormalised sum (as printed),
                          1 = the mean over Lambda (an alternative reading) */
+  int pp_limiter;     /* Euler: 1 = scale every stage's reconstruction towards the
+                         cell average until rho, p >= eps at the points of a
+                         Gauss-Lobatto decomposition and the volume Gauss points
+                         (the BP/PP safeguard the paper cites; Zhang-Shu scaling) */
 } or_problem;
 
 int or_ncomp(const or_problem* P);

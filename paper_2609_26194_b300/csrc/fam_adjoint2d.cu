@@ -672,8 +672,8 @@ extern "C" fam_status fam_adjoint(fam_t h, long nsteps, double cfl, int ckpt_eve
   if (!h || !U0 || !dJdUT || !dJdU0) return FAM_E_INVAL;
   bool periodic = true;
   for (int q = 0; q < 4; ++q) periodic = periodic && h->geo.bc[q] == kBcPeriodic;
-  if (h->d != 2 || h->eq != FAM_EULER || h->prec != 64 || !periodic)
-    return fail(h, FAM_E_UNSUPPORTED, "the adjoint is built for 2D Euler, FP64, periodic grids");
+  if (h->d != 2 || h->eq != FAM_EULER || h->prec != 64 || !periodic || h->pp)
+    return fail(h, FAM_E_UNSUPPORTED, "the adjoint is built for 2D Euler, FP64, periodic grids, without the BP/PP safeguard");
   if (nsteps < 1 || ckpt_every < 1) return fail(h, FAM_E_INVAL, "nsteps and ckpt_every must be >= 1");
   const Geo& g = h->geo;
   const long long n = (long long)g.nx * g.ny;

@@ -228,7 +228,7 @@ static void free_fused(fam_handle* h) {
 }
 
 static bool use_fused(const fam_handle* h) {
-  return h->fused_oe && h->d == 2 && h->oe_type != 1 && h->fz_ready && h->ops.fused;
+  return h->fused_oe && h->d == 2 && h->oe_type != 1 && !h->pp && h->fz_ready && h->ops.fused;
 }
 
 static fam_status build_fused(fam_handle* h) {
@@ -276,10 +276,21 @@ static fam_status enqueue_fused(fam_handle* h) {
   return FAM_OK;
 }
 
+// BP/PP safeguard: scaling factors of the stage input (2D) and, before the
+// first stage, the step size from the limited point speeds
+static fam_status pp_prep(fam_handle* h, int b, bool want_dt) {
+  if (!h->pp) return FAM_OK;
+  FAM_CUDA(h, h->ops.pp_prep(h, b, want_dt));
+  return FAM_OK;
+}
+
 static fam_status enqueue_step(fam_handle* h) {
+  if (fam_status p = pp_prep(h, 0, true)) return p;
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
+  if (fam_status p = pp_prep(h, 1, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   if (use_fused(h)) return enqueue_fused(h);
+  if (fam_status p = pp_prep(h, 2, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   fam_status s = enqueue_typeI(h, 1);
   if (s) return s;
@@ -304,8 +315,10 @@ static fam_status enqueue_step_profiled(fam_handle* h) {
     if (!e[q]) return fail(h, FAM_E_CUDA, "cudaEventCreate failed");
   }
   FAM_CUDA(h, cudaEventRecord(e[0], h->stream));
+  if (fam_status p = pp_prep(h, 0, true)) return p;
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
   FAM_CUDA(h, cudaEventRecord(e[1], h->stream));
+  if (fam_status p = pp_prep(h, 1, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   FAM_CUDA(h, cudaEventRecord(e[2], h->stream));
   h->prof_fused.push_back(use_fused(h) ? 1 : 0);
@@ -316,6 +329,7 @@ static fam_status enqueue_step_profiled(fam_handle* h) {
     FAM_CUDA(h, cudaEventRecord(e[4], h->stream));
     return FAM_OK;
   }
+  if (fam_status p = pp_prep(h, 2, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   FAM_CUDA(h, cudaEventRecord(e[3], h->stream));
   fam_status s = enqueue_typeI(h, 1);
@@ -332,10 +346,13 @@ fam_status fam_internal_step_fixed_dt(fam_handle* h, double dt, void* const* sto
   const size_t sb = h->buf_elems * h->elem;
   FAM_CUDA(h, cudaMemcpyAsync(&h->ctl->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[0], h->buf[0], sb, cudaMemcpyDeviceToDevice, h->stream));
+  if (fam_status p = pp_prep(h, 0, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[1], h->buf[1], sb, cudaMemcpyDeviceToDevice, h->stream));
+  if (fam_status p = pp_prep(h, 1, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[2], h->buf[2], sb, cudaMemcpyDeviceToDevice, h->stream));
+  if (fam_status p = pp_prep(h, 2, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[3], h->buf[1], sb, cudaMemcpyDeviceToDevice, h->stream));
   fam_status st = enqueue_typeI(h, 1);
@@ -404,6 +421,7 @@ void fam_destroy(fam_t h) {
   free_fused(h);
   for (int b = 0; b < 3; ++b)
     if (h->buf[b]) cudaFree(h->buf[b]);
+  if (h->theta) cudaFree(h->theta);
   if (h->ctl) cudaFree(h->ctl);
   if (h->t1_partial) cudaFree(h->t1_partial);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -635,6 +653,18 @@ fam_status fam_set_option(fam_t h, const char* key, double v) {
     if (h->d != 2) return fail(h, FAM_E_INVAL, "tile2d applies to 2D grids");
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, FAM_E_INVAL, "tile2d must be 0, 1 or 2");
     return select_tile(h, (int)v);
+  } else if (k == "pp_limiter") {
+    if (v != 0.0 && v != 1.0) return fail(h, FAM_E_INVAL, "pp_limiter must be 0 or 1");
+    if (v != 0.0 && h->eq != FAM_EULER) return fail(h, FAM_E_UNSUPPORTED, "pp_limiter is built for the Euler equations");
+    if (v != 0.0 && h->d == 2 && !h->theta) {
+      FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+      if (cudaMalloc(&h->theta, 2 * (size_t)h->geo.plane * h->elem) != cudaSuccess)
+        return fail(h, FAM_E_NOMEM, "no memory for the scaling factors");
+      // the factors of cells -1..n are written before each use; cells further
+      // out only feed faces outside the grid
+      FAM_CUDA(h, cudaMemsetAsync(h->theta, 0, 2 * (size_t)h->geo.plane * h->elem, h->stream));
+    }
+    h->pp = (int)v;
   } else if (k == "fused_oe") {
     if (h->d != 2) return fail(h, FAM_E_INVAL, "fused_oe applies to 2D grids");
     if (v != 0.0 && v != 1.0) return fail(h, FAM_E_INVAL, "fused_oe must be 0 or 1");
@@ -863,6 +893,7 @@ fam_status fam_residual(fam_t h, const void* U, void* R, int on_device) {
   if (fam_status b = check_bc(h)) return b;
   fam_status s = copy_in(h, U, on_device, 1);
   if (s) return s;
+  if ((s = pp_prep(h, 1, false))) return s;
   FAM_CUDA(h, h->ops.stage(h, 1, 1, 2, 0));
   return copy_out(h, R, on_device, 2);
 }

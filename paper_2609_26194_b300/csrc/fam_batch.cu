@@ -62,7 +62,51 @@ __device__ __forceinline__ Geo geo_of(const BatchInst& I, int bc) {
   return g;
 }
 
-template <typename T, class PH, int TX>
+// BP/PP safeguard (Euler): the largest spectral radius at the check points
+// of the limited reconstructions of the cells of every tile of A, into each
+// instance's speed maximum (the safeguard's CFL speeds; fam_pp.cuh).
+template <typename T, class PH, int TX, int NP, int HX>
+__device__ __forceinline__ void pp_speed_pass(const BatchInst* __restrict__ inst, const int4* __restrict__ tiles,
+                                              int ntiles, const T* A, BatchCtl* ictl, const PH& ph, T* tile,
+                                              double* red) {
+  constexpr int NC = PH::NC;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    const BatchInst I = inst[td.x];
+    __syncthreads();
+    load_tile_plain<T, TX>(tile, A, I, NP, td.y);
+    __syncthreads();
+    T m = T(0);
+    if (td.y + (int)threadIdx.x < I.nx) {
+      const int hx = threadIdx.x + 2;
+      auto cell = [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        T cf[NC][K];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) coef1d<T, K, HX>(tile, c, hx, cf[c]);
+        T avg[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) avg[c] = cf[c][0];
+        T tr, tt;
+        pp_limit_1d<T, K, NC>(cf, ph.gm1, tr, tt);
+        m = ph.speed_x(avg);
+        pp_points_1d<T, K, NC>(cf, [&](const T* u) { m = max_nonneg(m, ph.speed_x(u)); });
+      };
+      switch (I.k) {
+        case 3: cell(std::integral_constant<int, 3>{}); break;
+        case 4: cell(std::integral_constant<int, 4>{}); break;
+        case 5: cell(std::integral_constant<int, 5>{}); break;
+        default: cell(std::integral_constant<int, 6>{}); break;
+      }
+    }
+    const T bm = block_max<TX>(m, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, (double)bm);
+  }
+}
+
+// PP: the BP/PP safeguard (Euler) scales every stage's reconstructions and
+// sets the step sizes from the limited point speeds.
+template <typename T, class PH, int TX, bool PP = false>
 __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict__ inst,
                                                     const int4* __restrict__ tiles, int ntiles, int ninst,
                                                     T* A, T* B, T* C, BatchCtl* ictl, BatchGlobal* g, const PH ph,
@@ -89,6 +133,7 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
       m = block_max<TX>(m, red);
       if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, m);
     }
+    if constexpr (PP && NC == 3) pp_speed_pass<T, PH, TX, NP, HX>(inst, tiles, ntiles, A, ictl, ph, tile, red);
     if (!grid_barrier(g, nb)) return;
     for (int i = blockIdx.x * TX + threadIdx.x; i < ninst; i += nb * TX) {
       const double a = __longlong_as_double((long long)ictl[i].alpha_bits);
@@ -125,10 +170,10 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
           T* Uo = out + I.off;
           unsigned long long* nt = &ictl[td.x].ntrace;
           switch (I.k) {
-            case 3: stage1d_tile<T, 3, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
-            case 4: stage1d_tile<T, 4, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
-            case 5: stage1d_tile<T, 5, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
-            default: stage1d_tile<T, 6, PH, TX>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            case 3: stage1d_tile<T, 3, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            case 4: stage1d_tile<T, 4, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            case 5: stage1d_tile<T, 5, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            default: stage1d_tile<T, 6, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
           }
         } else {
           T* tr = faces;
@@ -146,6 +191,10 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
           if (threadIdx.x == 0) atomic_max_nonneg(&ictl[td.x].alpha_bits, (double)m);
         }
       }
+      if (!grid_barrier(g, nb)) return;
+    }
+    if constexpr (PP && NC == 3) {
+      pp_speed_pass<T, PH, TX, NP, HX>(inst, tiles, ntiles, A, ictl, ph, tile, red);
       if (!grid_barrier(g, nb)) return;
     }
     // per-instance clock and next step size
@@ -239,6 +288,7 @@ struct fam_batch {
   int tile_x = 128;
   int blocks_per_sm = 0;  // 0: occupancy maximum
   int grid = 0;
+  int pp = 0;                      // BP/PP safeguard (1D Euler)
   unsigned long long wait_ns = 0;  // grid-barrier wait limit (0: kWaitLimitNs)
   unsigned int barrier_extra = 0;  // test hook: arrivals the barrier waits for in vain
   void* buf[3] = {nullptr, nullptr, nullptr};
@@ -266,6 +316,8 @@ template <typename T, class PH, int TX>
 static cudaError_t launch_run(fam_batch* h, const PH& ph, long nsteps, double cfl, int init, bool query_only,
                               int* grid_out) {
   auto fn = batched1d_run<T, PH, TX>;
+  if constexpr (PH::NC == 3)
+    if (h->pp) fn = batched1d_run<T, PH, TX, true>;
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -546,6 +598,11 @@ fam_status fam_batch_set_option(fam_batch_t h, const char* key, double v) {
     return build_tiles(h);
   } else if (k == "blocks_per_sm") {
     h->blocks_per_sm = (int)v;
+  } else if (k == "pp_limiter") {
+    if (v != 0.0 && v != 1.0) return bfail(h, FAM_E_INVAL, "pp_limiter must be 0 or 1");
+    if (v != 0.0 && (h->d != 1 || h->eq != FAM_EULER))
+      return bfail(h, FAM_E_UNSUPPORTED, "pp_limiter is built for 1D Euler batches");
+    h->pp = (int)v;
   } else if (k == "wait_limit_ns" || k == "test_barrier_extra") {
     // read by the kernels from the batch's device block at run time: no
     // re-capture, and the step sizes stay valid

@@ -36,6 +36,11 @@ struct Ops {
   // -> A with U^n = A), and the resident blocks per SM of that kernel
   cudaError_t (*fused)(struct fam_handle*);
   cudaError_t (*fused_occupancy)(int* blocks_per_sm);
+  // BP/PP safeguard (Euler; option "pp_limiter"): before a stage reading
+  // buffer buf, the 2D scaling factors of its cells (theta buffer), and with
+  // want_dt the step size from the limited point speeds (1D: only the step
+  // size; the 1D stage kernel scales inline)
+  cudaError_t (*pp_prep)(struct fam_handle*, int buf, bool want_dt);
 };
 
 struct fam_handle {
@@ -83,6 +88,9 @@ struct fam_handle {
   unsigned int* fz_sync = nullptr;
   int fz_ntasks = 0, fz_ntiles = 0, fz_grid = 0;
   bool fz_ready = false;  // task list built for the current tile shape and sides
+  // BP/PP safeguard (option "pp_limiter"); 2D: scaling factors, 2 planes
+  int pp = 0;
+  void* theta = nullptr;
 };
 
 inline fam_status fail(fam_handle* h, fam_status s, const std::string& msg) {
@@ -162,8 +170,19 @@ struct Impl2D {
   }
   static cudaError_t stage(fam_handle* h, int in, int u0, int out, int s) {
     stage2d<T, K, PH, TX2, TY2><<<grid(h), TX2 * TY2, S::bytes_stage, h->stream>>>(
-        h->tm[in], h->tm_u0[u0], bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
+        h->tm[in], h->tm_u0[u0], bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s,
+        h->pp ? reinterpret_cast<const T*>(h->theta) : nullptr);
     return cudaGetLastError();
+  }
+  static cudaError_t pp_prep(fam_handle* h, int b, bool want_dt) {
+    if constexpr (PH::NC == 4) {
+      const long long n = (long long)(h->geo.nx + 2) * (h->geo.ny + 2);
+      const int blocks = (int)std::min<long long>((n + 127) / 128, 148LL * 8);
+      pp_theta2d<T, K, PH, 128><<<blocks, 128, 0, h->stream>>>(bufp<T>(h, b), reinterpret_cast<T*>(h->theta),
+                                                              h->geo, make_phys<T, PH>(h), h->ctl, want_dt ? 1 : 0);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
   }
   static cudaError_t oe(fam_handle* h, int in, int out, double dto) {
     oe2d<T, K, PH, TX2, TY2><<<grid(h), TX2 * TY2, S::bytes_oe, h->stream>>>(
@@ -186,13 +205,34 @@ struct Impl1D {
     cudaError_t e = cudaFuncSetAttribute(stage1d<T, K, PH, TX1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::bytes_stage);
     if (e != cudaSuccess) return e;
+    if constexpr (PH::NC == 3) {
+      e = cudaFuncSetAttribute(stage1d<T, K, PH, TX1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)S::bytes_stage);
+      if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(oe1d<T, K, PH, TX1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_oe);
   }
   static dim3 grid(const fam_handle* h) { return dim3((h->geo.nx + TX1 - 1) / TX1); }
   static cudaError_t stage(fam_handle* h, int in, int u0, int out, int s) {
+    if constexpr (PH::NC == 3) {
+      if (h->pp) {
+        stage1d<T, K, PH, TX1, true><<<grid(h), TX1, S::bytes_stage, h->stream>>>(
+            h->tm[in], bufp<T>(h, u0), bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
+        return cudaGetLastError();
+      }
+    }
     stage1d<T, K, PH, TX1><<<grid(h), TX1, S::bytes_stage, h->stream>>>(
         h->tm[in], bufp<T>(h, u0), bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
     return cudaGetLastError();
+  }
+  static cudaError_t pp_prep(fam_handle* h, int b, bool want_dt) {
+    if constexpr (PH::NC == 3) {
+      if (!want_dt) return cudaSuccess;  // the stage kernel scales inline
+      const int blocks = std::min((h->geo.nx + 127) / 128, 148 * 8);
+      pp_alpha1d<T, K, PH, 128><<<blocks, 128, 0, h->stream>>>(bufp<T>(h, b), h->geo, make_phys<T, PH>(h), h->ctl);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
   }
   static cudaError_t oe(fam_handle* h, int in, int out, double dto) {
     oe1d<T, K, PH, TX1><<<grid(h), TX1, S::bytes_oe, h->stream>>>(h->tm[in], bufp<T>(h, out), h->geo,
@@ -207,9 +247,11 @@ struct Impl1D {
   }
 };
 
-template <class I> Ops ops_of() { return Ops{0, 0, &I::stage, &I::oe, &I::alpha, &I::prepare, nullptr, nullptr}; }
+template <class I> Ops ops_of() {
+  return Ops{0, 0, &I::stage, &I::oe, &I::alpha, &I::prepare, nullptr, nullptr, &I::pp_prep};
+}
 template <class I> Ops ops_of2d() {
-  return Ops{I::kTX, I::kTY, &I::stage, &I::oe, &I::alpha, &I::prepare, &I::fused, &I::fused_occupancy};
+  return Ops{I::kTX, I::kTY, &I::stage, &I::oe, &I::alpha, &I::prepare, &I::fused, &I::fused_occupancy, &I::pp_prep};
 }
 
 // per-configuration selectors, one per instantiation unit (fam_inst.cu)

@@ -10,6 +10,7 @@
 #pragma once
 
 #include "fam_kernels2d.cuh"
+#include "fam_pp.cuh"
 
 namespace fam {
 
@@ -53,7 +54,9 @@ __device__ __forceinline__ void coef1d(const T* tile, int c, int hx, T* cf) {
 // at the instance's plane 0.  Called by all TX threads of the block.
 // ntrace (may be null) accumulates the faces of this tile at which a trace
 // has no spectral radius; each face of the grid is counted by one tile only.
-template <typename T, int K, class PH, int TX>
+// PP (Euler only): the stage's reconstructions are scaled by the BP/PP
+// safeguard (fam_pp.cuh) before any evaluation.
+template <typename T, int K, class PH, int TX, bool PP = false>
 __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const T* __restrict__ U0,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const T dt,
                                              const int stage, const int x0, unsigned long long* ntrace) {
@@ -66,16 +69,33 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
 #pragma unroll
   for (int q = 0; q < PH::NVA; ++q) VA[q] = T(0);
   T uq[NC][4];
+  if constexpr (PP && NC == 3) {
+    T cfa[NC][K];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    T cf[K];
-    coef1d<T, K, HX>(tile, c, hx, cf);
-    sym_pair<T, D, kRowInner>(cf, uq[c][2], uq[c][1]);
-    sym_pair<T, D, kRowOuter>(cf, uq[c][3], uq[c][0]);
-    T r, l;
-    sym_pair<T, D, kRowHalf>(cf, r, l);
-    fL[(tx + 1) * NC + c] = r;
-    fR[tx * NC + c] = l;
+    for (int c = 0; c < NC; ++c) coef1d<T, K, HX>(tile, c, hx, cfa[c]);
+    T tr, tt;
+    pp_limit_1d<T, K, NC>(cfa, ph.gm1, tr, tt);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      sym_pair<T, D, kRowInner>(cfa[c], uq[c][2], uq[c][1]);
+      sym_pair<T, D, kRowOuter>(cfa[c], uq[c][3], uq[c][0]);
+      T r, l;
+      sym_pair<T, D, kRowHalf>(cfa[c], r, l);
+      fL[(tx + 1) * NC + c] = r;
+      fR[tx * NC + c] = l;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T cf[K];
+      coef1d<T, K, HX>(tile, c, hx, cf);
+      sym_pair<T, D, kRowInner>(cf, uq[c][2], uq[c][1]);
+      sym_pair<T, D, kRowOuter>(cf, uq[c][3], uq[c][0]);
+      T r, l;
+      sym_pair<T, D, kRowHalf>(cf, r, l);
+      fL[(tx + 1) * NC + c] = r;
+      fR[tx * NC + c] = l;
+    }
   }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
@@ -87,13 +107,28 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
   // ring: cell x0-1 (right trace -> face 0) and cell x0+TX (left trace -> face TX)
   if (tx < 2) {
     const int rh = tx == 0 ? 1 : TX + 2;
+    if constexpr (PP && NC == 3) {
+      T cfa[NC][K];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T cf[K], r, l;
-      coef1d<T, K, HX>(tile, c, rh, cf);
-      sym_pair<T, D, kRowHalf>(cf, r, l);
-      if (tx == 0) fL[c] = r;
-      else fR[TX * NC + c] = l;
+      for (int c = 0; c < NC; ++c) coef1d<T, K, HX>(tile, c, rh, cfa[c]);
+      T tr, tt;
+      pp_limit_1d<T, K, NC>(cfa, ph.gm1, tr, tt);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T r, l;
+        sym_pair<T, D, kRowHalf>(cfa[c], r, l);
+        if (tx == 0) fL[c] = r;
+        else fR[TX * NC + c] = l;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T cf[K], r, l;
+        coef1d<T, K, HX>(tile, c, rh, cf);
+        sym_pair<T, D, kRowHalf>(cf, r, l);
+        if (tx == 0) fL[c] = r;
+        else fR[TX * NC + c] = l;
+      }
     }
   }
   __syncthreads();
@@ -148,7 +183,7 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
 }
 
 
-template <typename T, int K, class PH, int TX>
+template <typename T, int K, class PH, int TX, bool PP = false>
 __global__ void __launch_bounds__(TX)
     stage1d(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ U0, T* __restrict__ Uout,
             const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
@@ -167,7 +202,7 @@ __global__ void __launch_bounds__(TX)
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;
-  stage1d_tile<T, K, PH, TX>(tile, fL, fR, U0, Uout, geo, ph, T(dtd), stage, x0, &ctl->ntrace);
+  stage1d_tile<T, K, PH, TX, PP>(tile, fL, fR, U0, Uout, geo, ph, T(dtd), stage, x0, &ctl->ntrace);
 }
 
 // OE on a staged tile (layout as for stage1d_tile); returns this thread's
@@ -345,6 +380,38 @@ __global__ void __launch_bounds__(NT) alpha1d(const T* __restrict__ U, const Geo
   mx = block_max<NT>(mx, red);
   if (threadIdx.x == 0) {
     atomic_max_nonneg(&ctl->alpha_bits[0], mx);
+    step_epilogue(ctl, gridDim.x, false);
+  }
+}
+
+// BP/PP safeguard (Euler): the largest spectral radius at the check points of
+// every cell's limited reconstruction of U -> ctl->dt (no time advance); the
+// CFL rule of the safeguard (fam_pp.cuh).
+template <typename T, int K, class PH, int NT>
+__global__ void __launch_bounds__(NT) pp_alpha1d(const T* __restrict__ U, const Geo geo, const PH ph,
+                                                  FamCtl* __restrict__ ctl) {
+  constexpr int NC = PH::NC, D = K - 1;
+  __shared__ double red[64];
+  T mx = T(0);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < geo.nx; i += gridDim.x * NT) {
+    T cf[NC][K];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T* pa = U + cell_index(geo, c * 2, 0, i);
+      const T* pm = U + cell_index(geo, c * 2 + 1, 0, i);
+      Recon1D<K>::coef(pa[-1], pa[0], pa[1], pm[-1], pm[0], pm[1], cf[c]);
+    }
+    T avg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) avg[c] = cf[c][0];
+    T tr, tt;
+    pp_limit_1d<T, K, NC>(cf, ph.gm1, tr, tt);
+    mx = max_nonneg(mx, ph.speed_x(avg));
+    pp_points_1d<T, K, NC>(cf, [&](const T* u) { mx = max_nonneg(mx, ph.speed_x(u)); });
+  }
+  const double m = (double)block_max<NT>(mx, red);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&ctl->alpha_bits[0], m);
     step_epilogue(ctl, gridDim.x, false);
   }
 }

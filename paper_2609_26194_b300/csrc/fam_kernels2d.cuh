@@ -15,6 +15,7 @@
 #pragma once
 
 #include "fam_phys.cuh"
+#include "fam_pp.cuh"
 #include "fam_recon.cuh"
 
 namespace fam {
@@ -188,7 +189,8 @@ template <typename T, int K, class PH, int TX, int TY, class U0Src>
 __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, T* xR, T* yB, T* yT,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const int stage,
                                              const T dt, const int x0, const int y0, const U0Src& u0src,
-                                             unsigned long long* ntrace, const T idx_, const T idy_) {
+                                             unsigned long long* ntrace, const T idx_, const T idy_,
+                                             const T* __restrict__ theta = nullptr) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int HX = S::HX, HY = S::HY;
@@ -211,6 +213,17 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   const int hx = tx + 2, hy = ty + 2;
   const T wg[4] = {T(famgen::kGaussW[0]), T(famgen::kGaussW[1]), T(famgen::kGaussW[2]), T(famgen::kGaussW[3])};
 
+  // the BP/PP safeguard's scaling factors of a cell (1: none); theta holds
+  // planes (theta_rho, theta) in the padded layout, filled for cells -1..n
+  auto pp_theta = [&](int ci, int cj, T& tr, T& tt) {
+    tr = tt = T(1);
+    if (theta != nullptr && ci >= -G && ci < geo.nx + G && cj >= -G && cj < geo.ny + G) {
+      const long long q = cell_index(geo, 0, cj, ci);
+      tr = theta[q];
+      tt = theta[geo.plane + q];
+    }
+  };
+
   // ---- phase A: reconstruction, volume terms, traces --------------------
   T coef[NC][NCOEF];
 #pragma unroll
@@ -218,6 +231,16 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     T A[9], X[9], Y[9];
     gather_patch<T, HX, HY>(tile, c, hx, hy, A, X, Y);
     Recon2D<K>::coef(A, X, Y, coef[c]);
+  }
+  if (theta != nullptr) {
+    T tr, tt;
+    pp_theta(x0 + tx, y0 + ty, tr, tt);
+#pragma unroll
+    for (int l = 1; l < NCOEF; ++l) {
+      coef[0][l] *= tr;
+#pragma unroll
+      for (int c = 1; c < NC; ++c) coef[c][l] *= tt;
+    }
   }
   T VA[PH::NVA];
 #pragma unroll
@@ -317,6 +340,15 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
         Y[q] = py[o];
       }
       Recon2D<K>::tr_xp(A, X, Y, t);
+      if (theta != nullptr) {  // the ring cell's scaled reconstruction: u_bar + theta (t - u_bar)
+        T tr, tt;
+        pp_theta(x0 + rx, y0 + ry, tr, tt);
+        const T th = c == 0 ? tr : tt;
+        if (th != T(1)) {  // unscaled traces stay bit-identical to the unlimited path
+#pragma unroll
+          for (int g = 0; g < 4; ++g) t[g] = fma(th, t[g] - A[4], A[4]);
+        }
+      }
 #pragma unroll
       for (int g = 0; g < 4; ++g) out[(g * NC + c) * fstride] = t[g];
     }
@@ -450,7 +482,8 @@ constexpr int stage_min_blocks() {
 template <typename T, int K, class PH, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
     stage2d(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_u0,
-            T* __restrict__ Uout, const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage) {
+            T* __restrict__ Uout, const Geo geo, const PH ph, FamCtl* __restrict__ ctl, const int stage,
+            const T* __restrict__ theta) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int NP = S::NP, HX = S::HX, HY = S::HY;
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   const U0FromSmem<T, TX, TY> u0src{u0s, bar + 1, ctl, want_u0};
   // (load_tile's barrier has made cst visible)
   stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, cst[0], x0, y0, u0src, &ctl->ntrace,
-                                 cst[1], cst[2]);
+                                 cst[1], cst[2], theta);
 }
 
 // ---------------------------------------------------------------------------
@@ -921,6 +954,56 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
     }
   }
   if (threadIdx.x == 0) step_epilogue(ctl, gridDim.x, true);
+}
+
+// BP/PP safeguard (Euler, fam_pp.cuh): the scaling factors of the limited
+// reconstruction of every cell -1..nx x -1..ny of U into theta (planes
+// theta_rho, theta; padded layout), and with want_dt the largest spectral
+// radii at the check points of the interior cells -> ctl->dt (no time
+// advance).
+template <typename T, int K, class PH, int NT>
+__global__ void __launch_bounds__(NT) pp_theta2d(const T* __restrict__ U, T* __restrict__ theta, const Geo geo,
+                                                  const PH ph, FamCtl* __restrict__ ctl, const int want_dt) {
+  constexpr int NC = PH::NC;
+  constexpr int NCOEF = Recon2D<K>::NCOEF;
+  __shared__ double red[64];
+  T mx = T(0), my = T(0);
+  const int wx = geo.nx + 2, wy = geo.ny + 2;
+  const long long n = (long long)wx * wy;
+  for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < n; q += (long long)gridDim.x * NT) {
+    const int i = (int)(q % wx) - 1, j = (int)(q / wx) - 1;
+    T coef[NC][NCOEF];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T A[9], X[9], Y[9];
+#pragma unroll
+      for (int s9 = 0; s9 < 9; ++s9) {
+        const int ii = i + s9 % 3 - 1, jj = j + s9 / 3 - 1;
+        A[s9] = U[cell_index(geo, c * 3 + 0, jj, ii)];
+        X[s9] = U[cell_index(geo, c * 3 + 1, jj, ii)];
+        Y[s9] = U[cell_index(geo, c * 3 + 2, jj, ii)];
+      }
+      Recon2D<K>::coef(A, X, Y, coef[c]);
+    }
+    const bool interior = i >= 0 && i < geo.nx && j >= 0 && j < geo.ny;
+    T tr, tt, sx = T(0), sy = T(0);
+    pp_cell_2d<T, K, PH>(coef, ph, tr, tt, want_dt && interior, sx, sy);
+    const long long o = cell_index(geo, 0, j, i);
+    theta[o] = tr;
+    theta[geo.plane + o] = tt;
+    if (want_dt && interior) {
+      mx = max_nonneg(mx, sx);
+      my = max_nonneg(my, sy);
+    }
+  }
+  if (!want_dt) return;  // uniform: no block reduction
+  const T bx = block_max<NT>(mx, red);
+  const T by = block_max<NT>(my, red + 32);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&ctl->alpha_bits[0], (double)bx);
+    atomic_max_nonneg(&ctl->alpha_bits[1], (double)by);
+    step_epilogue(ctl, gridDim.x, false);
+  }
 }
 
 // Max Rusanov speeds at cell averages -> ctl->dt (no time advance).

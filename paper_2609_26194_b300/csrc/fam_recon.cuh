@@ -16,8 +16,9 @@
 namespace fam {
 
 // Rows of famgen::kLegAt: P_a at the inner Gauss node, the outer Gauss node,
-// at 1/2 and at 0.  Gauss nodes ascending: {-outer, -inner, +inner, +outer}.
-enum { kRowInner = 0, kRowOuter = 1, kRowHalf = 2, kRowZero = 3 };
+// at 1/2, at 0, and at the interior node 1/(2 sqrt 5) of the 4-point
+// Gauss--Lobatto rule.  Gauss nodes ascending: {-outer, -inner, +inner, +outer}.
+enum { kRowInner = 0, kRowOuter = 1, kRowHalf = 2, kRowZero = 3, kRowLobatto = 4 };
 
 __host__ __device__ constexpr int cidx(int a, int b) { return (a + b) * (a + b + 1) / 2 + a; }
 

@@ -259,11 +259,12 @@ def gen():
     # basis values P_a at the two positive Gauss nodes and at 1/2
     pos = [nodes[2], nodes[3]]
     out.append("// P_a(x) for the monic orthogonal polynomials on [-1/2,1/2], a = 0..6, at")
-    out.append("// x = Gauss node 2 (inner positive), Gauss node 3 (outer positive), 1/2, 0.")
+    out.append("// x = Gauss node 2 (inner positive), Gauss node 3 (outer positive), 1/2, 0,")
+    out.append("// and the positive interior node 1/(2 sqrt 5) of the 4-point Gauss-Lobatto rule.")
     rows = []
-    for x in pos + [HALF, sp.Integer(0)]:
+    for x in pos + [HALF, sp.Integer(0), 1 / (2 * sp.sqrt(5))]:
         rows.append("{" + ", ".join(num_literal(sp.simplify(LEG[a].subs(XI, x))) for a in range(7)) + "}")
-    out.append("__device__ constexpr double kLegAt[4][7] = {" + ", ".join(rows) + "};")
+    out.append("__device__ constexpr double kLegAt[5][7] = {" + ", ".join(rows) + "};")
     out.append("}  // namespace famgen")
     out.append("")
     # 1D

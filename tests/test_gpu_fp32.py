@@ -1,7 +1,7 @@
 """FP32 path: its error against FP64 per workload, with the bounds it must stay under.
 
 The FP32 kernels are the FP64 kernels instantiated in float (same operation
-order, FP32 reciprocal/sqrt refinement).  Errors are relative max-norms of
+order; 1/x, sqrt and exp from the one-instruction hardware approximations).  Errors are relative max-norms of
 the cell averages per conserved component (max |a - b| / max |b|), against
 the FP64 oracle where it runs the whole problem, else against the GPU FP64
 path (held to the oracle at 1e-12 by the parity tests).  Each test prints
@@ -91,6 +91,34 @@ def test_euler_2d_200_steps_fp32_error(k, data):
     print(f"\nFP32 error, 2D Euler {data} {n}^2 k={k} 200 steps: max {e:.2e}, L1 {e1:.2e}")
     # rectangles: the max-norm error sits at the contact and shock fronts
     # (measured 2.9e-2 at 1024^2); the L1 error stays small
+    if data == "smooth":
+        assert e < 1e-5 and e1 < 1e-5
+    else:
+        assert e < 0.1 and e1 < 1e-3
+
+
+@pytest.mark.parametrize("k", [4, 6])
+@pytest.mark.parametrize("data", ["smooth", "rectangles"])
+def test_euler_2d_fp32_error_against_oracle(k, data):
+    """The same workloads on a 256^2 periodic grid, 200 steps, FP32 against
+    the FP64 oracle itself, with the oracle's step sizes (CFL rule of Sec. 4
+    on the oracle's state)."""
+    n = 256
+    if data == "smooth":
+        U = inputs.euler2d_smooth(n)
+    else:
+        U = inputs.euler2d_rectangles(n, seed=3, nrect=64, **inputs.ADMISSIBLE_RECT)
+    cfl = 0.4 if k == 4 else 0.55
+    s32, P = make(2, (n, n), k, "euler", "periodic", prec=32)
+    ref, dts = U.copy(), []
+    for _ in range(200):
+        dts.append(oracle.dt(P, ref, cfl))
+        ref = oracle.step(P, ref, dts[-1])
+    s32.set_state(U.astype(np.float32))
+    s32.run_fixed(np.array(dts))
+    got = s32.get_state()
+    e, e1 = avg_err(got, ref), avg_err_l1(got, ref)
+    print(f"\nFP32 error vs oracle, 2D Euler {data} {n}^2 k={k} 200 steps: max {e:.2e}, L1 {e1:.2e}")
     if data == "smooth":
         assert e < 1e-5 and e1 < 1e-5
     else:

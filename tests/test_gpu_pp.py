@@ -1,0 +1,235 @@
+"""The optional BP/PP safeguard (option pp_limiter) on the GPU against the oracle.
+
+Both sides scale each stage's reconstruction towards the cell average until
+the density and the pressure are admissible at the points of a
+Gauss--Lobatto decomposition and at the volume Gauss points (1D: inline in
+the stage kernel; 2D: a per-cell kernel writing the two scaling factors,
+read by the stage kernel for its cells and its ring), and take the CFL
+speeds at those points.  The scaling is a switch, so whole runs are held to
+the parity bar or, where the oracle's own rounding spread is larger, to 10x
+that spread (as for reading c21).  The limited states are built by
+cancellation down to densities and pressures 1e-10 of the average, so one
+residual moves by up to 5e-10 and one step size by up to 1e-8 (relative)
+under 2e-16 input noise: single residuals and step sizes are held to 10x
+that spread too, measured on the same data.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_26194_b300 import fam, inputs
+from test_gpu_parity import comp_err, make, rounding_spread, smooth_state
+
+pytestmark = pytest.mark.gpu
+
+PRINTED_1D = dict(rho=(0.1, 2.0), umax=1.0, p=(0.1, 10.0))
+# instances of the printed-range 1D batch (seed 4 + i) whose reconstructions the safeguard scales
+CASES_1D = [(29, 221, 5), (346, 143, 6)]
+
+
+def _noisy(U, seed):
+    return U * (1.0 + 2e-16 * np.random.default_rng(seed).standard_normal(U.shape))
+
+
+def residual_spread(P, U, want, seeds=(1, 2, 3)):
+    return max(comp_err(oracle.residual(P, _noisy(U, s)), want) for s in seeds)
+
+
+def dt_spread(P, U, cfl, want, seeds=(1, 2, 3)):
+    return max(abs(oracle.dt(P, _noisy(U, s), cfl) - want) / want for s in seeds)
+
+
+def _rect(nx, ny):
+    n = max(nx, ny)
+    return np.ascontiguousarray(inputs.euler2d_rectangles(n, seed=3, nrect=64)[:, :, :ny, :nx])
+
+
+@pytest.mark.parametrize("i,n,k", CASES_1D)
+def test_residual_1d_with_safeguard(i, n, k):
+    U = inputs.euler1d_riemann(n, seed=4 + i, **PRINTED_1D)
+    s, P = make(1, n, k, "euler", "outflow", pp_limiter=1)
+    P.pp_limiter = 1
+    got, want = s.residual(U), oracle.residual(P, U)
+    s.close()
+    spread = residual_spread(P, U, want)
+    P.pp_limiter = 0
+    assert not np.array_equal(want, oracle.residual(P, U))  # the safeguard acts on this data
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+
+
+@pytest.mark.parametrize("tile", [0, 2])
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_residual_2d_with_safeguard(k, tile):
+    """Rectangles at the shock-run ranges, 48 x 40 cells (ragged tiles): the
+    unlimited residual is not finite; the limited one matches the oracle's."""
+    U = _rect(48, 40)
+    s, P = make(2, (48, 40), k, "euler", "periodic", pp_limiter=1, tile2d=tile)
+    P.pp_limiter = 1
+    got, want = s.residual(U), oracle.residual(P, U)
+    s.close()
+    assert np.all(np.isfinite(want))
+    spread = residual_spread(P, U, want)
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_safeguard_changes_nothing_on_admissible_data(d):
+    n = 300 if d == 1 else (70, 45)
+    U = smooth_state(d, n, seed=6, amp=0.2)
+    outs = []
+    for pp in (0, 1):
+        s, _ = make(d, n, 5, "euler", "periodic", pp_limiter=pp)
+        outs.append(s.residual(U))
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_step_size_from_limited_point_speeds(d):
+    if d == 1:
+        i, n, k = CASES_1D[0]
+        U = inputs.euler1d_riemann(n, seed=4 + i, **PRINTED_1D)
+        s, P = make(1, n, k, "euler", "outflow", pp_limiter=1)
+    else:
+        U = _rect(48, 40)
+        s, P = make(2, (48, 40), 5, "euler", "periodic", pp_limiter=1)
+    P.pp_limiter = 1
+    s.set_state(U)
+    s.step(0.2)
+    s.sync()
+    t, _, _ = s.time()
+    s.close()
+    want = oracle.dt(P, U, 0.2)
+    spread = dt_spread(P, U, 0.2, want)
+    assert abs(t - want) <= max(1e-12, 10.0 * spread) * want, (t, want, spread)
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_printed_range_rectangles_20_steps_with_safeguard(k):
+    """The rectangles at the shock-run ranges advance 20 steps at the paper's
+    CFL (0.4 / 0.55), admissible throughout, with no face trace lacking a
+    spectral radius, and match the oracle within 10x its rounding spread."""
+    U = _rect(48, 40)
+    cfl = 0.4 if k == 4 else 0.55
+    s, P = make(2, (48, 40), k, "euler", "periodic", pp_limiter=1)
+    P.pp_limiter = 1
+    s.set_state(U)
+    s.run_steps(20, cfl)
+    s.sync()  # raises if any step left the admissible set
+    got = s.get_state()
+    assert s.nonphysical_traces() == 0
+    s.close()
+    want, spread = rounding_spread(P, U, cfl, nsteps=20)
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+
+
+@pytest.mark.parametrize("i,n,k", CASES_1D)
+def test_printed_range_riemann_1d_100_steps_with_safeguard(i, n, k):
+    U = inputs.euler1d_riemann(n, seed=4 + i, **PRINTED_1D)
+    s, P = make(1, n, k, "euler", "outflow", pp_limiter=1)
+    P.pp_limiter = 1
+    s.set_state(U)
+    s.run_steps(100, 1 / 12)
+    s.sync()
+    got = s.get_state()
+    s.close()
+    want, spread = rounding_spread(P, U, 1 / 12, nsteps=100)
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+
+
+def test_safeguard_in_fp32_keeps_the_rectangles_admissible():
+    U = _rect(48, 40).astype(np.float32)
+    s, _ = make(2, (48, 40), 5, "euler", "periodic", prec=32, pp_limiter=1)
+    s.set_state(U)
+    s.run_steps(20, 0.55)
+    s.sync()
+    s.close()
+
+
+def test_safeguard_options():
+    s, _ = make(2, (32, 16), 5, "adv", "periodic")
+    with pytest.raises(fam.FamError) as e:
+        s.set_option("pp_limiter", 1)
+    assert e.value.code == 7  # FAM_E_UNSUPPORTED: built for the Euler equations
+    s.close()
+    s, _ = make(2, (32, 16), 5, "euler", "periodic", pp_limiter=1, fused_oe=1)
+    U = smooth_state(2, (32, 16), seed=1, amp=0.2)
+    s.set_state(U)
+    s.set_option("profile", 1)
+    s.step(0.4)
+    ms, _ = s.profile()
+    assert ms[3] > 0.0  # the safeguard runs the final stage and the OE split
+    s.close()
+
+
+def test_printed_range_batch_completes_with_safeguard():
+    """A cut-down 1D batch of the Riemann generator at its printed ranges
+    (instances that stop without the safeguard included), CFL 1/12: every
+    instance completes 60 steps, each equal to its single-problem run with
+    the safeguard and within 10x the oracle's spread of the oracle's."""
+    rng = np.random.default_rng(4)
+    ns = np.rint(np.exp(rng.uniform(np.log(64), np.log(16384), 400))).astype(int)
+    ks = rng.integers(3, 7, 400)
+    pick = [i for i in range(400) if ns[i] <= 400][:20]
+    for i, _, _ in CASES_1D:
+        if i not in pick:
+            pick.append(i)
+    nx = [int(ns[i]) for i in pick]
+    kk = [int(ks[i]) for i in pick]
+    states = [inputs.euler1d_riemann(n, seed=4 + i, **PRINTED_1D) for n, i in zip(nx, pick)]
+    b = fam.Batch(nx, kk, bc=fam.OUTFLOW)
+    b.set_option("pp_limiter", 1)
+    b.set_state(states)
+    b.run(60, 1 / 12)
+    b.sync()
+    got = b.get_state()
+    _, _, steps = b.times()
+    b.close()
+    assert np.all(steps == 60)
+    for q in (0, len(pick) - 2, len(pick) - 1):
+        with fam.Solver(1, nx[q], k=kk[q], equation=fam.EULER, bc=fam.OUTFLOW, pp_limiter=1) as s:
+            s.set_state(states[q])
+            s.run_steps(60, 1 / 12)
+            s.sync()
+            single = s.get_state()
+        assert np.array_equal(got[q], single), q
+        P = oracle.Problem(d=1, nx=nx[q], k=kk[q], eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4, pp_limiter=1)
+        want, spread = rounding_spread(P, states[q], 1 / 12, nsteps=60)
+        assert comp_err(got[q], want) < max(1e-12, 10.0 * spread), (q, comp_err(got[q], want), spread)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_shu_osher_at_the_papers_cfl_with_safeguard(k):
+    """Example 4.4 (400 cells, inflow / outflow) at Sec. 4's C = 0.55 for
+    k = 3, 4, which the unlimited scheme cannot run (it leaves the admissible
+    set in the first step, in the oracle too): with the safeguard the GPU run
+    reaches T = 1.8 admissible, in the post-shock density band.  One step is
+    held to 10x the oracle's rounding spread; at T = 1.8 the OE switch makes
+    the run discontinuous in its data (reading c21), so the bar there is 10x
+    the oracle's spread over the whole run."""
+    n, cfl = 400, 0.55
+    st = inputs.shu_osher_inflow()
+    s = fam.Solver(1, n, box=(-5.0, 5.0, 0.0, 1.0), k=k, equation=fam.EULER, bc=fam.OUTFLOW, pp_limiter=1)
+    s.set_bc(0, fam.INFLOW, st)
+    P = oracle.Problem(d=1, nx=n, x0=-5.0, x1=5.0, k=k, eq=oracle.EULER,
+                       bc=(oracle.INFLOW,) + (oracle.OUTFLOW,) * 3, pp_limiter=1)
+    P.inflow = (tuple(float(v) for v in st) + (0.0,),) + ((0.0,) * 4,) * 3
+    U = inputs.shu_osher(n)
+    s.set_state(U)
+    s.run_steps(1, cfl)
+    s.sync()
+    want, spread = rounding_spread(P, U, cfl, nsteps=1)
+    got = s.get_state()
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+
+    s.set_state(U)
+    s.run(1.8, cfl)
+    s.sync()  # raises if a step left the admissible set
+    t, _, _ = s.time()
+    got = s.get_state()
+    s.close()
+    assert t == 1.8
+    want, spread = rounding_spread(P, U, cfl, T=1.8)
+    assert comp_err(got, want) < 10.0 * spread, (comp_err(got, want), spread)
+    rho = got[0, 0]
+    assert np.all(rho > 0.5) and 4.0 < rho.max() < 5.0
