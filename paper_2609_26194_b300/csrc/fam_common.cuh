@@ -441,6 +441,18 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// Warp-wide maximum of values >= 0 on their bit patterns (every lane of the
+// warp must call it; NaN or negative counts as 0); valid in every lane.
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+  long long b = __double_as_longlong(v);
+  if (!(b > 0 && b <= 0x7FF0000000000000ll)) b = 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long c = __shfl_xor_sync(0xffffffffu, b, o);
+    b = c > b ? c : b;
+  }
+  return __longlong_as_double(b);
+}
+
 // Block-wide maximum of values >= 0 (speeds, |u|, deviations), on their bit
 // patterns with integer operations (the FP64 pipe stays free, which matters
 // most to the FP32 kernels).  A NaN or negative input counts as 0, as fmax

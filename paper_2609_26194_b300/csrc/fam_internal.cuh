@@ -177,8 +177,8 @@ struct Impl2D {
   static cudaError_t pp_prep(fam_handle* h, int b, bool want_dt) {
     if constexpr (PH::NC == 4) {
       const long long n = (long long)(h->geo.nx + 2) * (h->geo.ny + 2);
-      const int blocks = (int)std::min<long long>((n + 127) / 128, 148LL * 8);
-      pp_theta2d<T, K, PH, 128><<<blocks, 128, 0, h->stream>>>(bufp<T>(h, b), reinterpret_cast<T*>(h->theta),
+      const int blocks = (int)std::min<long long>((n + 63) / 64, 148LL * 16);
+      pp_theta2d<T, K, PH, 64><<<blocks, 64, 0, h->stream>>>(bufp<T>(h, b), reinterpret_cast<T*>(h->theta),
                                                               h->geo, make_phys<T, PH>(h), h->ctl, want_dt ? 1 : 0);
       return cudaGetLastError();
     }

@@ -202,10 +202,15 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   // conflicts): x-faces (row, col) with col 0..TX, y-faces (row, col) with
   // row 0..TY.  The x-faces col < TX are stored row-major with pitch TX and
   // the last column (col = TX) after them, so that a warp's two rows of a
-  // 16-wide tile fill 32 consecutive words.
+  // 16-wide tile fill 32 consecutive words.  Within a row the columns are
+  // rotated by the row index (col -> (col + row) mod TX): the ring's column
+  // 0 of every row then falls in distinct banks, and a row's last column
+  // (stored at TX * TY + row, bank row) fills the one bank that its other
+  // TX - 1 faces leave free.
+  static_assert((TX & (TX - 1)) == 0, "TX must be a power of 2");
   constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
   auto XI = [](int row, int col, int g, int c) {
-    return (g * NC + c) * NFX + (col < TX ? row * TX + col : TX * TY + row);
+    return (g * NC + c) * NFX + (col < TX ? row * TX + ((col + row) & (TX - 1)) : TX * TY + row);
   };
   auto YI = [](int row, int col, int g, int c) { return (g * NC + c) * NFY + row * TX + col; };
 
@@ -307,26 +312,33 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   //   bottom ring cell needs tr_yp = tr_xp of u(y, x)        (x- and y-moments swap)
   //   top ring cell    needs tr_ym = tr_xp of u(y, -x)       (swap; new x-moment = -old y-moment)
   // with the Gauss points in the same ascending order.  All lanes run one
-  // code path; only the gather offsets differ.
+  // code path; only the gather offsets differ.  Tasks run rows first, then
+  // columns; in FP32 each component's tasks are padded to whole warps, so
+  // that a warp gathers from one ring segment (a row: consecutive words; a
+  // column: rows HX apart) and its neighbour component's rows do not share
+  // its banks.  FP64 is not padded: an idle lane still costs its warp a
+  // full FP64 instruction.
   {
     constexpr int NR = 2 * (TX + TY);
-    for (int task = threadIdx.x; task < NR * NC; task += NT) {
-      const int r = task % NR, c = task / NR;
+    constexpr int NRP = sizeof(T) == 4 ? (NR + 31) / 32 * 32 : NR;
+    for (int task = threadIdx.x; task < NRP * NC; task += NT) {
+      const int r = task % NRP, c = task / NRP;
+      if (r >= NR) continue;
       int rx, ry, ox, oy, swap, fstride;
       unsigned long long xsign;
       T* out;
-      if (r < TY) {  // left column: its right trace = left side of x-face 0
-        rx = -1; ry = r; ox = 1; oy = HX; swap = 0; xsign = 0ull; fstride = NFX;
-        out = xL + XI(ry, 0, 0, 0);
-      } else if (r < 2 * TY) {  // right column: its left trace = right side of x-face TX
-        rx = TX; ry = r - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; fstride = NFX;
-        out = xR + XI(ry, TX, 0, 0);
-      } else if (r < 2 * TY + TX) {  // bottom row: its top trace = bottom side of y-face 0
-        rx = r - 2 * TY; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; fstride = NFY;
+      if (r < TX) {  // bottom row: its top trace = bottom side of y-face 0
+        rx = r; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; fstride = NFY;
         out = yB + YI(0, rx, 0, 0);
-      } else {  // top row: its bottom trace = top side of y-face TY
-        rx = r - 2 * TY - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; fstride = NFY;
+      } else if (r < 2 * TX) {  // top row: its bottom trace = top side of y-face TY
+        rx = r - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; fstride = NFY;
         out = yT + YI(TY, rx, 0, 0);
+      } else if (r < 2 * TX + TY) {  // left column: its right trace = left side of x-face 0
+        rx = -1; ry = r - 2 * TX; ox = 1; oy = HX; swap = 0; xsign = 0ull; fstride = NFX;
+        out = xL + XI(ry, 0, 0, 0);
+      } else {  // right column: its left trace = right side of x-face TX
+        rx = TX; ry = r - 2 * TX - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; fstride = NFX;
+        out = xR + XI(ry, TX, 0, 0);
       }
       const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + (ry + 2) * HX + (rx + 2);
       const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * HY * HX + (ry + 2) * HX + (rx + 2);
@@ -395,7 +407,8 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
       bool own;
       if (it < NXP) {
         const int f = it - (it / NFX) * NFX;
-        const int row = f < TX * TY ? f / TX : f - TX * TY, col = f < TX * TY ? f % TX : TX;
+        const int row = f < TX * TY ? f / TX : f - TX * TY;
+        const int col = f < TX * TY ? ((f % TX) - row) & (TX - 1) : TX;
         const int F = x0 + col;
         own = y0 + row < geo.ny && F <= geo.nx && (col < TX || F == geo.nx);
       } else {
@@ -570,18 +583,22 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
 #pragma unroll
     for (int f = 0; f < 4; ++f) fc[FI(f, c, q)] = t[f];
   }
-  for (int task = threadIdx.x; task < NR * NC; task += NT) {
-    const int r = task % NR, c = task / NR;
+  // rows first, then columns; FP32 pads each component's tasks to whole
+  // warps (one ring segment per warp, as in stage2d_tile)
+  constexpr int NRP = sizeof(T) == 4 ? (NR + 31) / 32 * 32 : NR;
+  for (int task = threadIdx.x; task < NRP * NC; task += NT) {
+    const int r = task % NRP, c = task / NRP;
+    if (r >= NR) continue;
     int rx, ry, ox, oy, swap, slot;
     unsigned long long xsign;
-    if (r < TY) {  // left ring column: its right trace
-      rx = -1; ry = r; ox = 1; oy = HX; swap = 0; xsign = 0ull; slot = 1;
-    } else if (r < 2 * TY) {  // right ring column: its left trace
-      rx = TX; ry = r - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; slot = 0;
-    } else if (r < 2 * TY + TX) {  // bottom ring row: its top trace
-      rx = r - 2 * TY; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; slot = 3;
-    } else {  // top ring row: its bottom trace
-      rx = r - 2 * TY - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; slot = 2;
+    if (r < TX) {  // bottom ring row: its top trace
+      rx = r; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; slot = 3;
+    } else if (r < 2 * TX) {  // top ring row: its bottom trace
+      rx = r - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; slot = 2;
+    } else if (r < 2 * TX + TY) {  // left ring column: its right trace
+      rx = -1; ry = r - 2 * TX; ox = 1; oy = HX; swap = 0; xsign = 0ull; slot = 1;
+    } else {  // right ring column: its left trace
+      rx = TX; ry = r - 2 * TX - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; slot = 0;
     }
     const int off = (ry + 2) * HX + (rx + 2);
     const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + off;
@@ -966,34 +983,65 @@ __global__ void __launch_bounds__(NT) pp_theta2d(const T* __restrict__ U, T* __r
                                                   const PH ph, FamCtl* __restrict__ ctl, const int want_dt) {
   constexpr int NC = PH::NC;
   constexpr int NCOEF = Recon2D<K>::NCOEF;
+  static_assert(NC * NCOEF * NT * sizeof(T) <= 48 * 1024, "coefficient slots exceed static shared memory");
   __shared__ double red[64];
+  __shared__ T cslot[NC * NCOEF * NT];  // this thread's coefficients, lane fastest
   T mx = T(0), my = T(0);
   const int wx = geo.nx + 2, wy = geo.ny + 2;
   const long long n = (long long)wx * wy;
-  for (long long q = blockIdx.x * (long long)NT + threadIdx.x; q < n; q += (long long)gridDim.x * NT) {
-    const int i = (int)(q % wx) - 1, j = (int)(q / wx) - 1;
-    T coef[NC][NCOEF];
+  // the loop bound is uniform over the block, so every lane of a warp takes
+  // part in the warp maxima below
+  for (long long q0 = blockIdx.x * (long long)NT; q0 < n; q0 += (long long)gridDim.x * NT) {
+    const long long q = q0 + threadIdx.x;
+    double px = 0.0, py = 0.0;  // this cell's speed maxima, published for the screen of later cells
+    if (q < n) {
+      const int i = (int)(q % wx) - 1, j = (int)(q / wx) - 1;
+      // coefficients: deviation bounds and the average here; a copy in this
+      // thread's shared-memory slot for the cells whose points are needed
+      T avg[NC], d[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T A[9], X[9], Y[9];
+      for (int c = 0; c < NC; ++c) {
+        T A[9], X[9], Y[9], cf[NCOEF];
 #pragma unroll
-      for (int s9 = 0; s9 < 9; ++s9) {
-        const int ii = i + s9 % 3 - 1, jj = j + s9 / 3 - 1;
-        A[s9] = U[cell_index(geo, c * 3 + 0, jj, ii)];
-        X[s9] = U[cell_index(geo, c * 3 + 1, jj, ii)];
-        Y[s9] = U[cell_index(geo, c * 3 + 2, jj, ii)];
+        for (int s9 = 0; s9 < 9; ++s9) {
+          const int ii = i + s9 % 3 - 1, jj = j + s9 / 3 - 1;
+          A[s9] = U[cell_index(geo, c * 3 + 0, jj, ii)];
+          X[s9] = U[cell_index(geo, c * 3 + 1, jj, ii)];
+          Y[s9] = U[cell_index(geo, c * 3 + 2, jj, ii)];
+        }
+        Recon2D<K>::coef(A, X, Y, cf);
+        avg[c] = cf[0];
+        d[c] = pp_dev_bound_2d<T, K>(cf);
+#pragma unroll
+        for (int l = 0; l < NCOEF; ++l) cslot[(c * NCOEF + l) * NT + threadIdx.x] = cf[l];
       }
-      Recon2D<K>::coef(A, X, Y, coef[c]);
+      const bool interior = i >= 0 && i < geo.nx && j >= 0 && j < geo.ny;
+      const bool speeds = want_dt && interior;
+      T run_x = T(0), run_y = T(0);
+      if (speeds) {  // maxima reached so far (exact values of T, so the conversion is exact)
+        run_x = T(__longlong_as_double((long long)__ldcg(&ctl->alpha_bits[0])));
+        run_y = T(__longlong_as_double((long long)__ldcg(&ctl->alpha_bits[1])));
+      }
+      T tr, tt, sx = T(0), sy = T(0);
+      const auto cf = [&](int c) { return SlotRef<T, NT>{cslot + c * NCOEF * NT + threadIdx.x}; };
+      pp_cell_2d<T, K, PH>(avg, d, cf, ph, tr, tt, speeds, run_x, run_y, sx, sy);
+      const long long o = cell_index(geo, 0, j, i);
+      theta[o] = tr;
+      theta[geo.plane + o] = tt;
+      if (speeds) {
+        mx = max_nonneg(mx, sx);
+        my = max_nonneg(my, sy);
+        px = (double)sx;
+        py = (double)sy;
+      }
     }
-    const bool interior = i >= 0 && i < geo.nx && j >= 0 && j < geo.ny;
-    T tr, tt, sx = T(0), sy = T(0);
-    pp_cell_2d<T, K, PH>(coef, ph, tr, tt, want_dt && interior, sx, sy);
-    const long long o = cell_index(geo, 0, j, i);
-    theta[o] = tr;
-    theta[geo.plane + o] = tt;
-    if (want_dt && interior) {
-      mx = max_nonneg(mx, sx);
-      my = max_nonneg(my, sy);
+    if (want_dt) {
+      px = warp_max_nonneg(px);
+      py = warp_max_nonneg(py);
+      if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&ctl->alpha_bits[0], px);
+        atomic_max_nonneg(&ctl->alpha_bits[1], py);
+      }
     }
   }
   if (!want_dt) return;  // uniform: no block reduction

@@ -35,6 +35,8 @@ template <typename T> struct PPEps;
 template <> struct PPEps<double> {
   static __device__ __forceinline__ double rho(double rb) { return fmin(1e-13, rb); }
   static __device__ __forceinline__ double p_frac() { return 1e-10; }
+  // relative margin of the screen's bounds for the rounding of point values
+  static __device__ __forceinline__ double tol() { return 1e-12; }
 };
 // FP32: the density target too is a fraction of the average, since
 // rho_bar + theta (rho - rho_bar) carries a rounding error of order
@@ -42,7 +44,31 @@ template <> struct PPEps<double> {
 template <> struct PPEps<float> {
   static __device__ __forceinline__ float rho(float rb) { return 1e-4f * rb; }
   static __device__ __forceinline__ float p_frac() { return 1e-4f; }
+  static __device__ __forceinline__ float tol() { return 2e-5f; }
 };
+
+// Bound of |p(x) - u_bar| over the cell for one component, from its
+// coefficients: sum over l >= 1 of |c_l| max|phi_l|.  A monic Legendre
+// polynomial on [-1/2, 1/2] is largest in modulus at the ends, so
+// max|P_a| = P_a(1/2) (> 0) and max|P_a P_b| <= P_a(1/2) P_b(1/2).
+template <typename T, int K>
+__device__ __forceinline__ T pp_dev_bound_1d(const T* c) {
+  T d = T(0);
+#pragma unroll
+  for (int a = 1; a < K; ++a) d = fma(fabs(c[a]), T(famgen::kLegAt[kRowHalf][a]), d);
+  return d;
+}
+template <typename T, int K>
+__device__ __forceinline__ T pp_dev_bound_2d(const T* c) {
+  T d = T(0);
+#pragma unroll
+  for (int sdeg = 1; sdeg < K; ++sdeg)
+#pragma unroll
+    for (int a = 0; a <= sdeg; ++a)
+      d = fma(fabs(c[cidx(a, sdeg - a)]),
+              T(famgen::kLegAt[kRowHalf][a] * famgen::kLegAt[kRowHalf][sdeg - a]), d);
+  return d;
+}
 
 // Row of the interior Lobatto node(s) for order K
 template <int K> struct LobRow {
@@ -102,6 +128,41 @@ struct PPCell {
     t1 = t2 = T(1);
     rmin = ub[0];
     pmin = pb;
+  }
+  // True if every point of the cell is certainly above both targets, from
+  // deviation bounds d[c] >= |p_c(x) - ub[c]| (pp_dev_bound_*), with a margin
+  // tol for the rounding of the point values: pass 1 would then find no
+  // point below target, so theta = 1 without evaluating the points.
+  __device__ __forceinline__ bool screen(const T* d) const {
+    if (bad_avg) return false;
+    const T tol = PPEps<T>::tol();
+    const T rlo = ub[0] - d[0] - tol * (ub[0] + d[0]);
+    if (!(rlo > eps)) return false;
+    T mh = fabs(ub[1]) + d[1];
+    T m2 = mh * mh;
+    if (NC == 4) {
+      mh = fabs(ub[2]) + d[2];
+      m2 = fma(mh, mh, m2);
+    }
+    // (the margin tol also covers the last-place errors of Fast<T>)
+    const T kin = T(0.5) * m2 * Fast<T>::rcp(rlo);
+    const T plo = gm1 * (ub[NC - 1] - d[NC - 1] - kin) - tol * gm1 * (fabs(ub[NC - 1]) + d[NC - 1] + kin);
+    return plo > epsp;
+  }
+  // Upper bounds of the x / y Rusanov speeds |v_dir| + c anywhere in a cell
+  // that passed the screen (density bounded away from 0 there).
+  __device__ __forceinline__ void speed_bound(const T* d, T gamma, T& bx, T& by) const {
+    const T tol = PPEps<T>::tol();
+    const T rlo = ub[0] - d[0] - tol * (ub[0] + d[0]);
+    const T rhi = ub[0] + d[0] + tol * (ub[0] + d[0]);
+    const T mxh = fabs(ub[1]) + d[1], myh = NC == 4 ? fabs(ub[2]) + d[2] : T(0);
+    const T mxl = fmax(fabs(ub[1]) - d[1], T(0)), myl = NC == 4 ? fmax(fabs(ub[2]) - d[2], T(0)) : T(0);
+    const T irlo = Fast<T>::rcp(rlo);
+    const T phi = gm1 * (ub[NC - 1] + d[NC - 1] - T(0.5) * fma(mxl, mxl, myl * myl) * Fast<T>::rcp(rhi));
+    const T c = Fast<T>::sqrt_(fmax(gamma * phi * irlo, T(0)));
+    const T f = T(1) + T(8) * tol;
+    bx = fma(mxh, irlo, c) * f;
+    by = fma(myh, irlo, c) * f;
   }
   // pass 1: the unlimited values
   __device__ __forceinline__ void first(const T* u) {
@@ -164,8 +225,13 @@ __device__ __forceinline__ void pp_limit_1d(T (&cf)[NC][K], T gm1, T& th_rho, T&
 #pragma unroll
   for (int c = 0; c < NC; ++c) avg[c] = cf[c][0];
   s.init(avg, gm1);
-  pp_points_1d<T, K, NC>(cf, [&](const T* u) { s.first(u); });
-  if (s.need_second()) pp_points_1d<T, K, NC>(cf, [&](const T* u) { s.second(u); });
+  T d[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) d[c] = pp_dev_bound_1d<T, K>(cf[c]);
+  if (!s.screen(d)) {  // a cell that passes the screen keeps theta = 1 without its points
+    pp_points_1d<T, K, NC>(cf, [&](const T* u) { s.first(u); });
+    if (s.need_second()) pp_points_1d<T, K, NC>(cf, [&](const T* u) { s.second(u); });
+  }
   th_rho = s.theta_rho();
   th = s.theta();
   if (th_rho != T(1) || th != T(1)) {
@@ -181,14 +247,22 @@ __device__ __forceinline__ void pp_limit_1d(T (&cf)[NC][K], T gm1, T& th_rho, T&
 // ---------------------------------------------------------------------------
 // 2D: check points from the coefficients of the 4 components
 // ---------------------------------------------------------------------------
+// Coefficient l of a component held in a shared-memory slot with stride NT
+// (one slot per thread, lane fastest).
+template <typename T, int NT>
+struct SlotRef {
+  const T* p;
+  __device__ __forceinline__ T operator[](int l) const { return p[l * NT]; }
+};
+
 // Points on the eta lines +-node(EROW); x at the rows listed (Gauss always,
-// the Lobatto rows when LOBX).
-template <typename T, int K, int EROW, bool LOBX, class F>
-__device__ __forceinline__ void pp_eta_line(const T (&coef)[4][K * (K + 1) / 2], F& f) {
+// the Lobatto rows when LOBX).  cf(c) gives component c's coefficients.
+template <typename T, int K, int EROW, bool LOBX, class CF, class F>
+__device__ __forceinline__ void pp_eta_line(const CF& cf, F& f) {
   constexpr int D = K - 1;
   T dp[4][D + 1], dm[4][D + 1];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) eta_pair<T, D, EROW>(coef[c], dp[c], dm[c]);
+  for (int c = 0; c < 4; ++c) eta_pair<T, D, EROW>(cf(c), dp[c], dm[c]);
   T a[4], b[4], e[4], g[4];
   auto xrow = [&](auto rowc) {
     constexpr int R = decltype(rowc)::value;
@@ -210,43 +284,65 @@ __device__ __forceinline__ void pp_eta_line(const T (&coef)[4][K * (K + 1) / 2],
   }
 }
 
-template <typename T, int K, class F>
-__device__ __forceinline__ void pp_points_2d(const T (&coef)[4][K * (K + 1) / 2], F&& f) {
-  pp_eta_line<T, K, kRowInner, true>(coef, f);  // Gauss eta: Gauss and Lobatto x
-  pp_eta_line<T, K, kRowOuter, true>(coef, f);
-  pp_eta_line<T, K, kRowHalf, false>(coef, f);  // Lobatto eta: Gauss x
-  pp_eta_line<T, K, LobRow<K>::row, false>(coef, f);
+template <typename T, int K, class CF, class F>
+__device__ __forceinline__ void pp_points_2d(const CF& cf, F&& f) {
+  pp_eta_line<T, K, kRowInner, true>(cf, f);  // Gauss eta: Gauss and Lobatto x
+  pp_eta_line<T, K, kRowOuter, true>(cf, f);
+  pp_eta_line<T, K, kRowHalf, false>(cf, f);  // Lobatto eta: Gauss x
+  pp_eta_line<T, K, LobRow<K>::row, false>(cf, f);
 }
 
-// (theta_rho, theta) of one 2D Euler cell, and optionally the largest x / y
-// spectral radii at the check points of the limited reconstruction.
-template <typename T, int K, class PH>
-__device__ __forceinline__ void pp_cell_2d(const T (&coef)[4][K * (K + 1) / 2], const PH& ph, T& th_rho, T& th,
-                                           bool want_speeds, T& sx_max, T& sy_max) {
+// (theta_rho, theta) of one 2D Euler cell from its average and deviation
+// bounds d (pp_dev_bound_2d), and optionally the largest x / y spectral
+// radii at the check points of the limited reconstruction.  A cell that
+// passes the screen gets theta = 1 without its points; with want_speeds, its
+// points are skipped too when its speed bounds do not exceed run_x / run_y,
+// values the grid's maxima already reached (they only grow, so the maxima
+// come out the same).  Only a cell that needs its points reads its
+// coefficients, through cf(c) (component c, indexable by coefficient).
+template <typename T, int K, class PH, class CF>
+__device__ __forceinline__ void pp_cell_2d(const T* avg, const T* d, const CF& cf, const PH& ph, T& th_rho, T& th,
+                                           bool want_speeds, T run_x, T run_y, T& sx_max, T& sy_max) {
   PPCell<T, 4> s;
-  const T avg[4] = {coef[0][0], coef[1][0], coef[2][0], coef[3][0]};
   s.init(avg, ph.gm1);
-  pp_points_2d<T, K>(coef, [&](const T* u) { s.first(u); });
-  if (s.need_second()) pp_points_2d<T, K>(coef, [&](const T* u) { s.second(u); });
+  const bool clear = s.screen(d);
+  bool skip = true;
+  if (want_speeds) {
+    ph.speeds(avg, sx_max, sy_max);
+    skip = false;
+    if (clear) {
+      T bx, by;
+      s.speed_bound(d, ph.g, bx, by);
+      skip = bx <= run_x && by <= run_y;
+    }
+  }
+  if (!clear || !skip) {
+    if (!clear) {
+      pp_points_2d<T, K>(cf, [&](const T* u) { s.first(u); });
+      if (s.need_second()) pp_points_2d<T, K>(cf, [&](const T* u) { s.second(u); });
+    }
+    if (!skip) {
+      const T tr = s.theta_rho(), tt = s.theta();
+      const bool unit = tr == T(1) && tt == T(1);
+      pp_points_2d<T, K>(cf, [&](const T* u) {
+        T w[4];
+        if (unit) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) w[c] = u[c];
+        } else {
+          w[0] = fma(tr, u[0] - avg[0], avg[0]);
+#pragma unroll
+          for (int c = 1; c < 4; ++c) w[c] = fma(tt, u[c] - avg[c], avg[c]);
+        }
+        T bx, by;
+        ph.speeds(w, bx, by);
+        sx_max = max_nonneg(sx_max, bx);
+        sy_max = max_nonneg(sy_max, by);
+      });
+    }
+  }
   th_rho = s.theta_rho();
   th = s.theta();
-  if (want_speeds) {
-    T ax, ay;
-    ph.speeds(avg, ax, ay);
-    sx_max = ax;
-    sy_max = ay;
-    const T tr = th_rho, tt = th;
-    pp_points_2d<T, K>(coef, [&](const T* u) {
-      T w[4];
-      w[0] = fma(tr, u[0] - avg[0], avg[0]);
-#pragma unroll
-      for (int c = 1; c < 4; ++c) w[c] = fma(tt, u[c] - avg[c], avg[c]);
-      T bx, by;
-      ph.speeds(w, bx, by);
-      sx_max = max_nonneg(sx_max, bx);
-      sy_max = max_nonneg(sy_max, by);
-    });
-  }
 }
 
 }  // namespace fam

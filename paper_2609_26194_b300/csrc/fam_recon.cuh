@@ -44,8 +44,10 @@ __device__ __forceinline__ void sym_pair(const T* d, T& vp, T& vm) {
 }
 
 // 2D: partial sums over eta at eta = +/- node(ROW): dp[a] = sum_b c_ab P_b(+y).
-template <typename T, int D, int ROW>
-__device__ __forceinline__ void eta_pair(const T* c, T* dp, T* dm) {
+// c is anything indexable by the coefficient index (an array, a pointer, a
+// strided view of shared memory).
+template <typename T, int D, int ROW, typename C>
+__device__ __forceinline__ void eta_pair(const C& c, T* dp, T* dm) {
 #pragma unroll
   for (int a = 0; a <= D; ++a) {
     T e = c[cidx(a, 0)];
