@@ -51,6 +51,10 @@ UNIT = "cell-stage/s"
 # (its reciprocals and roots are single hardware operations in FP32, a few
 # FLOP fewer per cell).
 FLOP_PER_CELL_STAGE = {(5, 64): 2847.2, (5, 32): 2847.2}
+# FP64-unit instructions (DFMA + DADD + DMUL) per cell of one stage launch,
+# counted by ncu on the same capture: the FP64 unit's own busy fraction is
+# these at one instruction per FP64 lane and cycle (half the FLOP peak).
+FP64_UNIT_INST_PER_CELL = {(5, 64): 1793.8}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
 # dram__bytes_write.sum of the current kernel, 1.1833 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
@@ -72,6 +76,8 @@ def parse():
                     help="2D tile shape: the autotuner's pick, or an index into fam.TILES_2D")
     ap.add_argument("--fused", default="0", choices=["0", "1"],
                     help="with a fixed --tile: 1 runs the final stage and the OE as one fused launch")
+    ap.add_argument("--pp", action="store_true",
+                    help="run the workload with the BP/PP safeguard (option pp_limiter) on")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain report")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-plain report")
@@ -88,7 +94,8 @@ def parse():
 
 def workload_config(a):
     return {"workload": f"2D Euler FAM{a.k} periodic {a.n}x{a.n}, smooth density wave "
-                        f"rho=1+0.2sin(2pi(x+y)), u=v=p=1, CFL {cfl_of(a)}, Type-II OE",
+                        f"rho=1+0.2sin(2pi(x+y)), u=v=p=1, CFL {cfl_of(a)}, Type-II OE"
+                        + (", BP/PP safeguard on" if getattr(a, "pp", False) else ""),
             "grid": [a.n, a.n], "k": a.k, "equation": "euler2d", "gamma": 1.4, "oe": "type2",
             "cells": a.n * a.n, "bytes_per_state": 4 * 3 * a.n * a.n * (a.precision // 8),
             "l2": "state buffers (>= 1.6 GB) far larger than L2; no flush needed"}
@@ -672,7 +679,7 @@ def run_fam(a):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = fam.Solver(2, n, n, k=k, equation=fam.EULER, bc=fam.PERIODIC, precision=prec,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, pp_limiter=1 if a.pp else 0)
     dev = torch.from_numpy(U).cuda()
     s.set_state(dev)
     # the library's tile autotuner (a few probe steps per tile shape, untimed)
@@ -740,8 +747,14 @@ def run_fam(a):
         achieved = fpc * cells / (stage_ms * 1e-3)
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak_flops, "traffic": (traffic * cells if traffic else None),
+                "frac_is": "algorithmic FLOP of the method (products on the integer pipes included) / "
+                           f"measured FP{prec} FMA peak",
                 "peak_source": f"measured FP{prec} FMA loop on this GPU (fam_alu_peak), live in this run",
                 "kernel": "stage2d", "kernel_ms": stage_ms}
+        ipc = FP64_UNIT_INST_PER_CELL.get((k, prec))
+        if ipc is not None:  # the FP64 unit's own occupancy: its instructions against half the FLOP peak
+            roof["fp64_unit"] = {"instructions_per_cell": ipc,
+                                 "frac": ipc * cells / (stage_ms * 1e-3) / (peak_flops / 2.0)}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak_flops / 1e12, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": "stage2d", "kernel_ms": stage_ms}
@@ -767,7 +780,7 @@ def run_fam(a):
                            "stage3_oe_fused": kern_ms[2] / max(1, prof_steps)} if fused else
                           {"stage1": kern_ms[0] / max(1, prof_steps), "stage2": kern_ms[1] / max(1, prof_steps),
                            "stage3": kern_ms[2] / max(1, prof_steps), "oe": oe_ms}),
-            "e2e": e2e, "gpu_launches": (3 if fused else 4) * a.steps, "clocks": ck}
+            "e2e": e2e, "gpu_launches": ((3 if fused else 4) + (3 if a.pp else 0)) * a.steps, "clocks": ck}
     if rank == 0 and world == 1 and not a.no_batched:
         line["batched"] = batched_report(a, torch)
         line["batched2d"] = batched2d_report(a, torch)

@@ -159,10 +159,11 @@ fam_status fam_run_fixed(fam_t h, long nsteps, const double* dts);
 
 /* Autotuner (not in the paper): times probe_steps steps of each 2D tile
  * shape, with the final stage and OE split and fused (option "fused_oe";
- * split only for Type-I OE), on the handle's current state (restored
- * afterwards, clock included), keeps the fastest and appends it to
- * cache_path (if not NULL) keyed by GPU name, equation, order, precision
- * and grid; a cached entry is reused without timing.  *choice (may be NULL)
+ * split only for Type-I OE or with "pp_limiter"), on the handle's current
+ * state (restored afterwards, clock included), keeps the fastest and
+ * appends it to cache_path (if not NULL) keyed by GPU name, equation,
+ * order, precision, grid and the safeguard; a cached entry is reused
+ * without timing.  *choice (may be NULL)
  * receives tile2d + 3 * fused_oe (0..5).  1D handles have one shape and no
  * fused path (choice 0).  Synchronous. */
 fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path, int* choice);

@@ -550,7 +550,8 @@ fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
   char key[512];
-  std::snprintf(key, sizeof(key), "%s|2d|eq%d|k%d|p%d|%dx%d", prop.name, h->eq, h->k, h->prec, h->geo.nx, h->geo.ny);
+  std::snprintf(key, sizeof(key), "%s|2d|eq%d|k%d|p%d|%dx%d%s", prop.name, h->eq, h->k, h->prec, h->geo.nx,
+                h->geo.ny, h->pp ? "|pp" : "");
   if (cache_path && cache_path[0]) {
     FILE* f = std::fopen(cache_path, "r");
     if (f) {
@@ -562,7 +563,7 @@ fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path
         if (std::strcmp(line, key) == 0) {
           const int t = std::atoi(tab + 1);
           std::fclose(f);
-          if (t < 0 || t > 5 || (t > 2 && h->oe_type == 1)) break;
+          if (t < 0 || t > 5 || (t > 2 && (h->oe_type == 1 || h->pp))) break;
           if (choice) *choice = t;
           h->fused_oe = t / 3;
           fam_status st = select_tile(h, t % 3);
@@ -585,8 +586,8 @@ fam_status fam_tune(fam_t h, double cfl, int probe_steps, const char* cache_path
   const int fused_was = h->fused_oe;
   int best = h->tile2d + 3 * fused_was;
   float best_ms = 1e30f;
-  // candidates: every tile shape, split and (Type II / no OE) fused
-  const int nfused = h->oe_type == 1 ? 1 : 2;
+  // candidates: every tile shape, split and (Type II / no OE, no safeguard) fused
+  const int nfused = (h->oe_type == 1 || h->pp) ? 1 : 2;
   for (int cand = 0; cand < 3 * nfused && s == FAM_OK; ++cand) {
     const int t = cand % 3;
     if (select_tile(h, t) != FAM_OK) continue;
