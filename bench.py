@@ -544,7 +544,7 @@ def configs_report(a, torch):
     s.close()
     return {"unit": UNIT, "note": "each run: CUDA events around one graph-captured multi-step launch "
                                   "(after an untimed run of the same length)", "runs": out,
-            "rectangles_printed_ranges": printed_rectangles_report(torch)}
+            "rectangles_printed_ranges": printed_rectangles_report(torch), "extreme_1d": extreme_1d_report(torch)}
 
 
 def printed_rectangles_report(torch, n: int = 4096, max_steps: int = 20):
@@ -603,6 +603,39 @@ def printed_rectangles_report(torch, n: int = 4096, max_steps: int = 20):
                                            "nonphysical_traces": s.nonphysical_traces(),
                                            "value": 3.0 * n * n * max_steps / sec, "unit": UNIT, "seconds": sec}
         s.close()
+    return out
+
+
+def extreme_1d_report(torch):
+    """Example 4.7's extreme 1D tests (Sedov point blast on [-2, 2] to
+    T = 1e-3, LeBlanc tube on [-10, 10] to T = 1e-4, outflow) with the BP/PP
+    safeguard at the CFL of its guarantee, FP64: complete runs through
+    fam_run (16-step graph chunks, synchronised between chunks), host wall
+    clock.  The unlimited scheme stops in the first step on both."""
+    from paper_2609_26194_b300 import fam, inputs
+    out = {}
+    for name, gen, n, x0, x1, T in (("sedov", inputs.sedov_1d, 801, -2.0, 2.0, 1e-3),
+                                    ("leblanc", inputs.leblanc_1d, 800, -10.0, 10.0, 1e-4)):
+        U = gen(n)
+        for k in (3, 5, 6):
+            cfl = 1 / 6 if k <= 4 else 1 / 12
+            s = fam.Solver(1, n, box=(x0, x1, 0.0, 1.0), k=k, equation=fam.EULER, bc=fam.OUTFLOW, pp_limiter=1)
+            s.set_state(U)
+            s.run(T / 20, cfl)  # builds the chunk graph
+            s.set_state(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                nst = s.run(T, cfl)
+                s.sync()
+                status = "completed"
+            except fam.FamError as e:
+                nst, status = s.time()[2], str(e)
+            sec = time.perf_counter() - t0
+            t, _, _ = s.time()
+            out[f"{name}_k{k}"] = {"cells": n, "cfl": cfl, "T": T, "t": t, "steps": nst, "status": status,
+                                   "seconds": sec, "value": 3.0 * n * nst / sec, "unit": UNIT}
+            s.close()
     return out
 
 

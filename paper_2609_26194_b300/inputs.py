@@ -292,6 +292,34 @@ def lax_tube(n: int = 200, gamma: float = GAMMA) -> np.ndarray:
     return project_1d(f, n, -0.5, 0.5, nq=8)
 
 
+def sedov_1d(n: int = 801, gamma: float = GAMMA) -> np.ndarray:
+    """Sedov point blast of Example 4.7 on [-2, 2]: rho = 1, u = 0, total
+    energy 1e-12 everywhere except the central cell (n odd: the cell around
+    x = 0), whose energy density is 3.2e6 / dx.  Cell averages, zero first
+    moments."""
+    if n % 2 == 0:
+        raise ValueError("n must be odd (one central cell)")
+    dx = 4.0 / n
+    U = np.zeros((3, 2, n))
+    U[0, 0] = 1.0
+    U[2, 0] = 1e-12
+    U[2, 0, n // 2] = 3.2e6 / dx
+    return U
+
+
+def leblanc_1d(n: int = 800, gamma: float = GAMMA) -> np.ndarray:
+    """LeBlanc shock tube of Example 4.7 on [-10, 10]: (rho, u, p) =
+    (2, 0, 1e9) for x < 0 and (1e-3, 0, 1) for x > 0 (the jump on a face for
+    even n); cell averages, zero first moments."""
+    if n % 2:
+        raise ValueError("n must be even (the jump on a cell face)")
+    U = np.zeros((3, 2, n))
+    h = n // 2
+    U[0, 0, :h], U[0, 0, h:] = 2.0, 1e-3
+    U[2, 0, :h], U[2, 0, h:] = 1e9 / (gamma - 1.0), 1.0 / (gamma - 1.0)
+    return U
+
+
 # smooth accuracy data (Example 4.1 and Example 4.2 of the paper)
 
 def burgers_smooth(n: int) -> np.ndarray:

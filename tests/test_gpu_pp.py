@@ -233,3 +233,62 @@ def test_shu_osher_at_the_papers_cfl_with_safeguard(k):
     assert comp_err(got, want) < 10.0 * spread, (comp_err(got, want), spread)
     rho = got[0, 0]
     assert np.all(rho > 0.5) and 4.0 < rho.max() < 5.0
+
+
+EXTREME = {  # Example 4.7: generator, cells, domain, final time
+    "sedov": (inputs.sedov_1d, 201, -2.0, 2.0, 1e-3),
+    "leblanc": (inputs.leblanc_1d, 200, -10.0, 10.0, 1e-4),
+}
+
+
+@pytest.mark.parametrize("name", ["sedov", "leblanc"])
+@pytest.mark.parametrize("k", [3, 5, 6])
+def test_extreme_1d_tests_with_safeguard(name, k):
+    """Example 4.7 with the safeguard at the CFL of its guarantee, run to
+    the final time through fam_run: every step admissible, the oracle's
+    result within 10x its rounding spread (these runs are not sensitive:
+    the spread stays below 1e-13 at T), mass and energy conserved, the
+    Sedov profile mirror-symmetric."""
+    gen, n, x0, x1, T = EXTREME[name]
+    U = gen(n)
+    cfl = 1 / 6 if k <= 4 else 1 / 12
+    s = fam.Solver(1, n, box=(x0, x1, 0.0, 1.0), k=k, equation=fam.EULER, bc=fam.OUTFLOW, pp_limiter=1)
+    s.set_state(U)
+    s.run(T, cfl)
+    s.sync()
+    t, _, nst = s.time()
+    got = s.get_state()
+    s.close()
+    P = oracle.Problem(d=1, nx=n, x0=x0, x1=x1, k=k, eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4, pp_limiter=1)
+    want, spread = rounding_spread(P, U, cfl, T=T)
+    assert t == T
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+    for c in (0, 2):
+        assert abs(got[c, 0].sum() / U[c, 0].sum() - 1.0) < 1e-12
+    if name == "sedov":
+        rho = got[0, 0]
+        assert np.max(np.abs(rho - rho[::-1])) < 1e-12 * rho.max()
+
+
+def test_sedov_batch_with_safeguard_equals_single_runs():
+    """Sedov blasts at four resolutions and orders in one batch on [-2, 2],
+    safeguard on, CFL 1/12, 300 steps each with its own step size: each
+    instance equals its single-problem run bit for bit."""
+    ns, ks = [101, 201, 301, 401], [3, 4, 5, 6]
+    states = [inputs.sedov_1d(n) for n in ns]
+    b = fam.Batch(ns, ks, x0=-2.0, x1=2.0, bc=fam.OUTFLOW)
+    b.set_option("pp_limiter", 1)
+    b.set_state(states)
+    b.run(300, 1 / 12)
+    b.sync()
+    got = b.get_state()
+    _, _, steps = b.times()
+    b.close()
+    assert np.all(steps == 300)
+    for q, (n, k) in enumerate(zip(ns, ks)):
+        with fam.Solver(1, n, box=(-2.0, 2.0, 0.0, 1.0), k=k, equation=fam.EULER, bc=fam.OUTFLOW,
+                        pp_limiter=1) as s:
+            s.set_state(states[q])
+            s.run_steps(300, 1 / 12)
+            s.sync()
+            assert np.array_equal(got[q], s.get_state()), q

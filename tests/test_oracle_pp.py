@@ -14,7 +14,8 @@ with the CFL speeds taken at those points.  What fixes it, without any GPU:
   - the forward-Euler property it exists for: one Euler step of the averages
     at the bound CFL (dt from the limited point speeds) keeps every average
     admissible, on data where the unlimited scheme loses admissibility;
-  - whole runs at the printed shock-run ranges stay admissible with it and
+  - whole runs at the printed shock-run ranges, Shu-Osher at the paper's
+    CFL and the extreme tests of Example 4.7 stay admissible with it and
     fail without it.
 """
 import numpy as np
@@ -110,21 +111,43 @@ def test_printed_range_rectangles_run_with_the_safeguard(k):
         assert failed != ok, (k, pp)
 
 
-def test_sedov_like_blast_1d_stays_admissible():
-    """A 1D blast (the Sedov set-up of Example 4.6 in spirit: one cell of high
-    energy in a cold gas at rest, rho = 1, p = 1e-6 elsewhere), k = 5, 40
-    steps at the bound CFL: admissible with the safeguard."""
-    n = 101
-    prim_p = np.full(n, 1e-6)
-    prim_p[n // 2] = 0.4 * 3.2e4
-    U = np.zeros((3, 2, n))
-    U[0, 0] = 1.0
-    U[2, 0] = prim_p / 0.4
-    P = oracle.Problem(d=1, nx=n, x0=-2.0, x1=2.0, k=5, eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4, pp_limiter=1)
-    V = U.copy()
-    for _ in range(40):
-        V = oracle.step(P, V, oracle.dt(P, V, 1 / 12))
-        assert oracle.inadmissible(P, V) == 0
+EXTREME = {  # Example 4.7: generator, cells, domain, final time
+    "sedov": (inputs.sedov_1d, 201, -2.0, 2.0, 1e-3),
+    "leblanc": (inputs.leblanc_1d, 200, -10.0, 10.0, 1e-4),
+}
+
+
+@pytest.mark.parametrize("name", ["sedov", "leblanc"])
+@pytest.mark.parametrize("k", [3, 5])
+def test_extreme_1d_tests_run_with_the_safeguard(name, k):
+    """Example 4.7 (Sedov point blast on [-2, 2] to T = 1e-3; LeBlanc tube
+    on [-10, 10] to T = 1e-4; outflow), at the CFL of the guarantee (1/6 for
+    k = 3, 1/12 for k = 5).  The unlimited scheme leaves the admissible set
+    in its first step; with the safeguard every step stays admissible, mass
+    and energy are conserved to rounding (no wave reaches the boundary, whose
+    fluxes carry no mass or energy for gas at rest), the Sedov profile stays
+    mirror-symmetric, and its peak density lies below the strong-shock limit
+    (gamma + 1) / (gamma - 1) = 6."""
+    gen, n, x0, x1, T = EXTREME[name]
+    U = gen(n)
+    cfl = 1 / 6 if k <= 4 else 1 / 12
+    P0 = oracle.Problem(d=1, nx=n, x0=x0, x1=x1, k=k, eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4)
+    assert oracle.inadmissible(P0, oracle.step(P0, U, oracle.dt(P0, U, cfl)))
+    P = oracle.Problem(**{**P0.__dict__, "pp_limiter": 1})
+    V, t = U.copy(), 0.0
+    while t < T:
+        dt = min(oracle.dt(P, V, cfl), T - t)
+        V = oracle.step(P, V, dt)
+        t += dt
+        assert oracle.inadmissible(P, V) == 0, t
+    for c in (0, 2):  # mass, energy
+        assert abs(V[c, 0].sum() / U[c, 0].sum() - 1.0) < 1e-12
+    rho = V[0, 0]
+    if name == "sedov":
+        assert np.max(np.abs(rho - rho[::-1])) < 1e-12 * rho.max()
+        assert 4.0 < rho.max() < 6.0
+    else:
+        assert rho.min() > 0.9e-3 and rho.max() < 2.02  # positivity, not a maximum principle
 
 
 def test_shu_osher_at_the_papers_cfl_runs_with_the_safeguard():
