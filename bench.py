@@ -544,7 +544,8 @@ def configs_report(a, torch):
     s.close()
     return {"unit": UNIT, "note": "each run: CUDA events around one graph-captured multi-step launch "
                                   "(after an untimed run of the same length)", "runs": out,
-            "rectangles_printed_ranges": printed_rectangles_report(torch), "extreme_1d": extreme_1d_report(torch)}
+            "rectangles_printed_ranges": printed_rectangles_report(torch), "extreme_1d": extreme_1d_report(torch),
+            "double_mach": double_mach_report(torch)}
 
 
 def printed_rectangles_report(torch, n: int = 4096, max_steps: int = 20):
@@ -636,6 +637,75 @@ def extreme_1d_report(torch):
             out[f"{name}_k{k}"] = {"cells": n, "cfl": cfl, "T": T, "t": t, "steps": nst, "status": status,
                                    "seconds": sec, "value": 3.0 * n * nst / sec, "unit": UNIT}
             s.close()
+    return out
+
+
+def double_mach_report(torch, nx: int = 1440, ny: int = 480):
+    """Example 4.8, double Mach reflection on [0, 3] x [0, 1] at the paper's
+    1440 x 480 mesh, FAM5 with the BP/PP safeguard at CFL 1/12 (the unlimited
+    scheme stops in its first step).  FP32: the complete run to T = 0.2
+    through fam_run (host wall clock).  FP64: 200 steps in one graph (CUDA
+    events) and one profiled step (stage launches include the safeguard's
+    factor kernel and the front ghosts); the complete FP64 run is projected
+    from the FP32 run's step count."""
+    from paper_2609_26194_b300 import fam, inputs
+    post, pre = inputs.double_mach_states()
+    U = inputs.double_mach(nx, ny)
+    cfl = 1.0 / 12.0
+
+    def solver(prec, stream=None):
+        s = fam.Solver(2, nx, ny, box=inputs.DMR_BOX, k=5, equation=fam.EULER, bc=fam.OUTFLOW, precision=prec,
+                       pp_limiter=1, stream=stream)
+        s.set_bc(0, fam.INFLOW, post)
+        s.set_bc(2, fam.REFLECTIVE)
+        s.set_bc_split(2, inputs.DMR_FRONT[0], post)
+        s.set_bc_front(3, *inputs.DMR_FRONT, post, pre)
+        return s
+
+    out = {"mesh": [nx, ny], "k": 5, "cfl": cfl, "T": 0.2}
+    s = solver(32)
+    U32 = U.astype(np.float32)
+    s.set_state(U32)
+    s.run(0.002, cfl)  # builds the chunk graph
+    s.set_state(U32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        nst = s.run(0.2, cfl)
+        s.sync()
+        status = "completed"
+    except fam.FamError as e:
+        nst, status = s.time()[2], str(e)
+    sec = time.perf_counter() - t0
+    rho = s.get_state()[0, 0]
+    out["f32_complete_run"] = {"status": status, "steps": nst, "seconds": sec,
+                               "value": 3.0 * nx * ny * nst / sec, "unit": UNIT,
+                               "rho_max": float(rho.max()), "rho_min": float(rho.min())}
+    s.close()
+    st = torch.cuda.Stream()
+    s = solver(64, st.cuda_stream)
+    s.set_state(U)
+    s.run_steps(200, cfl)
+    s.sync()
+    s.set_state(U)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.run_steps(200, cfl)
+    e1.record(st)
+    torch.cuda.synchronize()
+    s.sync()
+    ms = e0.elapsed_time(e1) / 200
+    s.set_option("profile", 1)
+    s.step(cfl)
+    prof, _ = s.profile()
+    s.close()
+    tot = sum(prof)
+    out["f64_200_steps"] = {"ms_per_step": ms, "value": 3.0 * nx * ny / (ms * 1e-3), "unit": UNIT,
+                            "profile_ms": {"stage1_with_dt": prof[0], "stage2": prof[1], "stage3": prof[2],
+                                           "oe": prof[3]},
+                            "oe_share": prof[3] / tot if tot > 0 else None,
+                            "projected_complete_run_seconds": ms * 1e-3 * nst}
     return out
 
 

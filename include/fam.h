@@ -122,10 +122,34 @@ fam_status fam_set_option(fam_t h, const char* key, double value);
  * moments zero).  Sides are set one at a time, so the combination is
  * checked when a step, residual or OE next uses it: a periodic side whose
  * opposite side is not periodic gives FAM_E_INVAL there, and an inflow side
- * next to a reflective wall FAM_E_UNSUPPORTED (not built).  Errors here:
+ * next to a reflective wall FAM_E_UNSUPPORTED (not built) unless the wall's
+ * split part (fam_set_bc_split) covers their shared corner.  Errors here:
  * FAM_E_INVAL (side or bc out of range, y sides of a 1D grid, inflow
  * without a state). */
 fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state);
+
+/* Split side (2D; the double Mach reflection of Example 4.8 imposes the
+ * post-shock state on the wall's part x < 1/6): the ghost cells of `side`
+ * whose nearest interior cell along the side (row for sides 0/1, column for
+ * sides 2/3) has its centre below `position` hold `state` (conservative
+ * averages, zero moments); the rest of the side keeps the condition set by
+ * fam_set_bc.  position at or below the side's start removes the split.
+ * Kept when fam_set_bc changes the side's condition.  Errors: FAM_E_INVAL
+ * (side out of range, a periodic side, no state), FAM_E_UNSUPPORTED (1D). */
+fam_status fam_set_bc_split(fam_t h, int side, double position, const double* state);
+
+/* Front condition of a y-side (2D; the top side of Example 4.8 follows the
+ * exact motion of the incident shock): a ghost cell of `side` with centre
+ * (x, y) holds `behind` if x < a + b y + c t and `ahead` otherwise
+ * (conservative averages, zero moments), t the time of the state the kernel
+ * reads: rewritten before every stage for its input's time (t, t + dt,
+ * t + dt/2 in SSP-RK3; the OE reads the state at t + dt).  fam_residual and
+ * fam_oe take the handle's current time.  The front side has no images
+ * (code 4 in the side's condition).  The fused final stage + OE runs split
+ * while a front side is set.  Errors: FAM_E_INVAL (a 1D grid, an x-side,
+ * missing states). */
+fam_status fam_set_bc_front(fam_t h, int side, double a, double b, double c, const double* behind,
+                            const double* ahead);
 
 /* Copy a state in (layout above).  on_device = 0: U is host memory;
  * 1: U is device memory of the handle's device.  Resets the clock to t = 0

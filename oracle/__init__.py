@@ -24,7 +24,7 @@ _HDR = os.path.join(_HERE, "fam_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
-PERIODIC, OUTFLOW, REFLECTIVE, INFLOW = 0, 1, 2, 3
+PERIODIC, OUTFLOW, REFLECTIVE, INFLOW, FRONT = 0, 1, 2, 3, 4
 OE_NONE, OE_TYPE1, OE_TYPE2 = 0, 1, 2
 
 
@@ -50,6 +50,8 @@ class _Problem(ctypes.Structure):
         ("gamma", ctypes.c_double), ("ax", ctypes.c_double), ("ay", ctypes.c_double),
         ("oe_type", ctypes.c_int), ("gamma_k", ctypes.c_double), ("oe_jump_q6", ctypes.c_int),
         ("oe_mean", ctypes.c_int), ("pp_limiter", ctypes.c_int),
+        ("split", ctypes.c_double * 4), ("front", ctypes.c_double * 3), ("front_ahead", ctypes.c_double * 4),
+        ("time", ctypes.c_double),
     ]
 
 
@@ -75,6 +77,10 @@ class Problem:
     oe_jump_q6: int = 1
     oe_mean: int = 0
     pp_limiter: int = 0
+    split: tuple = (0.0, 0.0, 0.0, 0.0)
+    front: tuple = (0.0, 0.0, 0.0)
+    front_ahead: tuple = (0.0,) * 4
+    time: float = 0.0
 
     @property
     def ncomp(self) -> int:
@@ -103,6 +109,12 @@ class Problem:
         p.oe_type, p.gamma_k, p.oe_jump_q6 = self.oe_type, self.gamma_k, self.oe_jump_q6
         p.oe_mean = self.oe_mean
         p.pp_limiter = self.pp_limiter
+        for q in range(4):
+            p.split[q] = float(self.split[q])
+            p.front_ahead[q] = float(self.front_ahead[q])
+        for q in range(3):
+            p.front[q] = float(self.front[q])
+        p.time = float(self.time)
         return p
 
 

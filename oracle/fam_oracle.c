@@ -295,19 +295,51 @@ static void ghost_from(const or_problem* P, padded* A, int gj, int gi, int sj, i
     }
 }
 
+/* Centre of interior cell i (clamped to the grid) along x, of row j along y. */
+static double centre_x(const or_problem* P, int i) {
+  if (i < 0) i = 0;
+  if (i > P->nx - 1) i = P->nx - 1;
+  return P->x0 + (i + 0.5) * (P->x1 - P->x0) / P->nx;
+}
+static double centre_y(const or_problem* P, int j) {
+  if (j < 0) j = 0;
+  if (j > P->ny - 1) j = P->ny - 1;
+  return P->y0 + (j + 0.5) * (P->y1 - P->y0) / P->ny;
+}
+
+/* The fixed state a ghost cell of side s holds, or NULL when the side's own
+ * condition applies there: the split part of the side (along-side centre
+ * below split[s]) and the front condition.  a = along-side index of the
+ * ghost cell, q = its layer (0 next to the grid). */
+static const double* side_state(const or_problem* P, int s, int a, int q) {
+  const double along = s < 2 ? centre_y(P, a) : centre_x(P, a);
+  if (P->split[s] > 0.0 && along < P->split[s]) return P->inflow[s];
+  if (P->bc[s] == OR_BC_FRONT) {
+    const double dy = (P->y1 - P->y0) / P->ny;
+    const double y = s == 2 ? P->y0 - (q + 0.5) * dy : P->y1 + (q + 0.5) * dy;
+    const double x = P->x0 + (a + 0.5) * (P->x1 - P->x0) / P->nx;  /* the ghost column's own centre */
+    return x < P->front[0] + P->front[1] * y + P->front[2] * P->time ? P->inflow[s] : P->front_ahead;
+  }
+  return NULL;
+}
+
 static void fill_ghosts(const or_problem* P, padded* A) {
   int nx = A->nx, ny = A->ny;
   /* x-direction, interior rows */
   for (int j = 0; j < ny; ++j)
     for (int q = 0; q < G; ++q) {
       int gl = -1 - q, gr = nx + q;
-      switch (P->bc[0]) {
+      const double* fl = side_state(P, 0, j, q);
+      const double* fr = side_state(P, 1, j, q);
+      if (fl) ghost_from(P, A, j, gl, j, 0, 0, 0, fl);
+      else switch (P->bc[0]) {
         case OR_BC_PERIODIC: ghost_from(P, A, j, gl, j, ((gl % nx) + nx) % nx, 0, 0, NULL); break;
         case OR_BC_OUTFLOW: ghost_from(P, A, j, gl, j, 0, 0, 0, NULL); break;
         case OR_BC_REFLECTIVE: ghost_from(P, A, j, gl, j, q < nx ? q : nx - 1, 0, 1, NULL); break;
         default: ghost_from(P, A, j, gl, j, 0, 0, 0, P->inflow[0]); break;
       }
-      switch (P->bc[1]) {
+      if (fr) ghost_from(P, A, j, gr, j, nx - 1, 0, 0, fr);
+      else switch (P->bc[1]) {
         case OR_BC_PERIODIC: ghost_from(P, A, j, gr, j, gr % nx, 0, 0, NULL); break;
         case OR_BC_OUTFLOW: ghost_from(P, A, j, gr, j, nx - 1, 0, 0, NULL); break;
         case OR_BC_REFLECTIVE: ghost_from(P, A, j, gr, j, nx - 1 - q >= 0 ? nx - 1 - q : 0, 0, 1, NULL); break;
@@ -319,13 +351,17 @@ static void fill_ghosts(const or_problem* P, padded* A) {
   for (int i = -G; i < nx + G; ++i)
     for (int q = 0; q < G; ++q) {
       int gl = -1 - q, gr = ny + q;
-      switch (P->bc[2]) {
+      const double* fb = side_state(P, 2, i, q);
+      const double* ft = side_state(P, 3, i, q);
+      if (fb) ghost_from(P, A, gl, i, 0, i, 1, 0, fb);
+      else switch (P->bc[2]) {
         case OR_BC_PERIODIC: ghost_from(P, A, gl, i, ((gl % ny) + ny) % ny, i, 1, 0, NULL); break;
         case OR_BC_OUTFLOW: ghost_from(P, A, gl, i, 0, i, 1, 0, NULL); break;
         case OR_BC_REFLECTIVE: ghost_from(P, A, gl, i, q < ny ? q : ny - 1, i, 1, 1, NULL); break;
         default: ghost_from(P, A, gl, i, 0, i, 1, 0, P->inflow[2]); break;
       }
-      switch (P->bc[3]) {
+      if (ft) ghost_from(P, A, gr, i, ny - 1, i, 1, 0, ft);
+      else switch (P->bc[3]) {
         case OR_BC_PERIODIC: ghost_from(P, A, gr, i, gr % ny, i, 1, 0, NULL); break;
         case OR_BC_OUTFLOW: ghost_from(P, A, gr, i, ny - 1, i, 1, 0, NULL); break;
         case OR_BC_REFLECTIVE: ghost_from(P, A, gr, i, ny - 1 - q >= 0 ? ny - 1 - q : 0, i, 1, 1, NULL); break;
@@ -921,17 +957,22 @@ int or_step(const or_problem* P, double* U, double dt) {
   if (!U0 || !Us || !R) { free(U0); free(Us); free(R); return -1; }
   memcpy(U0, U, sizeof(double) * n);
   int rc = 0;
-  /* stage 1: U1 = U0 + dt R(U0) */
-  rc |= or_residual(P, U0, R);
+  /* the stage states' times (they matter only to a front side condition) */
+  or_problem Q = *P;
+  /* stage 1: U1 = U0 + dt R(U0), U0 at time t */
+  rc |= or_residual(&Q, U0, R);
   for (size_t q = 0; q < n; ++q) Us[q] = U0[q] + dt * R[q];
-  /* stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt R(U1)) */
-  rc |= or_residual(P, Us, R);
+  /* stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt R(U1)), U1 at t + dt */
+  Q.time = P->time + dt;
+  rc |= or_residual(&Q, Us, R);
   for (size_t q = 0; q < n; ++q) Us[q] = 0.75 * U0[q] + 0.25 * (Us[q] + dt * R[q]);
-  /* stage 3: Un = 1/3 U0 + 2/3 (U2 + dt R(U2)) */
-  rc |= or_residual(P, Us, R);
+  /* stage 3: Un = 1/3 U0 + 2/3 (U2 + dt R(U2)), U2 at t + dt/2 */
+  Q.time = P->time + 0.5 * dt;
+  rc |= or_residual(&Q, Us, R);
   for (size_t q = 0; q < n; ++q) U[q] = 1.0 / 3.0 * U0[q] + 2.0 / 3.0 * (Us[q] + dt * R[q]);
-  /* end-of-step OE */
-  rc |= or_oe(P, dt, U, NULL);
+  /* end-of-step OE on the state at t + dt */
+  Q.time = P->time + dt;
+  rc |= or_oe(&Q, dt, U, NULL);
   free(U0);
   free(Us);
   free(R);
@@ -941,19 +982,21 @@ int or_step(const or_problem* P, double* U, double dt) {
 int or_run(const or_problem* P, double* U, double T, long nsteps, double cfl, int smooth, double* t_out,
            long* nsteps_out) {
   size_t n = state_len(P);
-  double t = 0.0;
+  double t = 0.0;  /* time since the start (the states' times are P->time + t) */
   long s = 0;
   int rc = 0;
+  or_problem Q = *P;
   for (;;) {
     if (T > 0.0) {
       if (t >= T) break;
     } else if (s >= nsteps) {
       break;
     }
-    double dt = or_dt(P, U, cfl, smooth);
+    Q.time = P->time + t;
+    double dt = or_dt(&Q, U, cfl, smooth);
     if (!(dt > 0.0) || !isfinite(dt)) { rc = -1; break; }
     if (T > 0.0 && t + dt >= T) dt = T - t;
-    if (or_step(P, U, dt)) { rc = -1; break; }
+    if (or_step(&Q, U, dt)) { rc = -1; break; }
     t = (T > 0.0 && t + dt >= T) ? T : t + dt;
     ++s;
     for (size_t q = 0; q < n; ++q)

@@ -26,7 +26,7 @@ extern "C" {
 #endif
 
 enum { OR_ADVECTION = 0, OR_BURGERS = 1, OR_EULER = 2 };
-enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_REFLECTIVE = 2, OR_BC_INFLOW = 3 };
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_REFLECTIVE = 2, OR_BC_INFLOW = 3, OR_BC_FRONT = 4 };
 enum { OR_OE_NONE = 0, OR_OE_TYPE1 = 1, OR_OE_TYPE2 = 2 };
 
 typedef struct {
@@ -48,6 +48,21 @@ typedef struct {
                          cell average until rho, p >= eps at the points of a
                          Gauss-Lobatto decomposition and the volume Gauss points
                          (the BP/PP safeguard the paper cites; Zhang-Shu scaling) */
+  /* Side conditions that vary along a side or in time (the double Mach
+   * reflection set-up of Example 4.8).  split[s] > 0: the ghost cells of
+   * side s whose cell centre along the side (x for the y-sides, y for the
+   * x-sides; ghost columns and rows take the centre of the nearest interior
+   * one) lies below split[s] hold inflow[s]; the others follow bc[s].
+   * bc[s] = OR_BC_FRONT (y-sides only): a ghost cell with centre (x, y) holds
+   * inflow[s] if x < front[0] + front[1] y + front[2] time, front_ahead
+   * otherwise (a straight front moving along x).  time: the time of the state
+   * passed to or_residual / or_oe / or_dt; or_step evaluates its stages at
+   * time, time + dt, time + dt/2 and the OE at time + dt; or_run starts at
+   * time. */
+  double split[4];
+  double front[3];
+  double front_ahead[4];
+  double time;
 } or_problem;
 
 int or_ncomp(const or_problem* P);

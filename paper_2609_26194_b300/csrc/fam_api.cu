@@ -65,7 +65,8 @@ __global__ void fill_ghosts_kernel(T* U, const Geo geo, int np) {
 }
 
 // Inflow ghosts (both layers of a side, corners included): the prescribed
-// averages, zero moments (Remark in Sec. 2.3).
+// averages, zero moments (Remark in Sec. 2.3).  A side with a split holds
+// them only where its nearest interior row / column lies below the split.
 template <typename T>
 __global__ void fill_inflow_kernel(T* U, const Geo geo, int side, int nc, const double4 st) {
   const int gx = geo.px, gy = geo.rows;
@@ -79,6 +80,10 @@ __global__ void fill_inflow_kernel(T* U, const Geo geo, int side, int nc, const 
     else if (side == 2) in = gy > 1 && y < G;
     else in = gy > 1 && y >= geo.ny + G && y < geo.ny + 2 * G;
     if (!in) continue;
+    if (geo.bc[side] != kBcInflow) {  // a split side: only its split part
+      const int along = side < 2 ? min(max(y - G, 0), geo.ny - 1) : min(max(x - G, 0), geo.nx - 1);
+      if (along >= geo.split[side]) continue;
+    }
     for (int c = 0; c < nc; ++c)
       for (int m = 0; m < geo.nm; ++m) U[(long long)(c * geo.nm + m) * geo.plane + q] = m == 0 ? T(sv[c]) : T(0);
   }
@@ -86,7 +91,7 @@ __global__ void fill_inflow_kernel(T* U, const Geo geo, int side, int nc, const 
 
 static fam_status fill_inflow(fam_handle* h) {
   for (int side = 0; side < 4; ++side) {
-    if (h->geo.bc[side] != kBcInflow) continue;
+    if (h->geo.bc[side] != kBcInflow && h->geo.split[side] <= 0) continue;
     const double* s = h->inflow[side];
     const double4 st = make_double4(s[0], s[1], s[2], s[3]);
     for (int b = 0; b < 3; ++b) {
@@ -96,6 +101,66 @@ static fam_status fill_inflow(fam_handle* h) {
         fill_inflow_kernel<float><<<148 * 4, 256, 0, h->stream>>>(bufp<float>(h, b), h->geo, side, h->nc, st);
       FAM_CUDA(h, cudaGetLastError());
     }
+  }
+  return FAM_OK;
+}
+
+// Front ghosts of a y-side (both layers, every column including the x-ghost
+// columns): the behind state where the ghost cell's centre (x, y) has
+// x < a + b y + c t, the ahead state elsewhere; zero moments.  t is the time
+// of the state in U: ctl->t + w ctl->dt, w = 0, 1, 1/2, 1 for the inputs of
+// stages 1, 2, 3 and of the OE (SSP-RK3 stage times).
+struct FrontArgs {
+  double a, b, c, x0, yb;  // yb: the side's boundary coordinate (y0 or y1)
+  double behind[4], ahead[4];
+  double w;                // stage-time weight of dt
+};
+template <typename T>
+__global__ void fill_front_kernel(T* U, const Geo geo, int side, int nc, const FrontArgs f, const FamCtl* ctl) {
+  // products and sums rounded one by one (no contraction), as a plain
+  // evaluation of the same expressions rounds them
+  const double t = __dadd_rn(ctl->t, __dmul_rn(f.w, ctl->dt));
+  const int n = geo.px * G;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int x = q % geo.px, layer = q / geo.px;  // layer 0 next to the grid
+    const int y = side == 2 ? G - 1 - layer : geo.ny + G + layer;
+    const double xc = __dadd_rn(f.x0, __dmul_rn(x - G + 0.5, geo.dx));
+    const double off = __dmul_rn(layer + 0.5, geo.dy);
+    const double yc = side == 2 ? __dsub_rn(f.yb, off) : __dadd_rn(f.yb, off);
+    const bool behind = xc < __dadd_rn(__dadd_rn(f.a, __dmul_rn(f.b, yc)), __dmul_rn(f.c, t));
+    const long long o = (long long)y * geo.px + x;
+    for (int c = 0; c < nc; ++c)
+      for (int m = 0; m < geo.nm; ++m)
+        U[(long long)(c * geo.nm + m) * geo.plane + o] = m == 0 ? T(behind ? f.behind[c] : f.ahead[c]) : T(0);
+  }
+}
+
+static bool has_front(const fam_handle* h) {
+  return h->d == 2 && (h->geo.bc[2] == kBcFront || h->geo.bc[3] == kBcFront);
+}
+
+// Rewrite the front ghosts of buffer b for the state at ctl->t + w ctl->dt.
+static fam_status fill_front(fam_handle* h, int b, double w) {
+  if (!has_front(h)) return FAM_OK;
+  for (int side = 2; side < 4; ++side) {
+    if (h->geo.bc[side] != kBcFront) continue;
+    FrontArgs f;
+    f.a = h->front[side][0];
+    f.b = h->front[side][1];
+    f.c = h->front[side][2];
+    f.x0 = h->grid.x0;
+    f.yb = side == 2 ? h->grid.y0 : h->grid.y1;
+    for (int c = 0; c < 4; ++c) {
+      f.behind[c] = h->inflow[side][c];
+      f.ahead[c] = h->front_ahead[side][c];
+    }
+    f.w = w;
+    const int blocks = (h->geo.px * G + 255) / 256;
+    if (h->prec == 64)
+      fill_front_kernel<double><<<blocks, 256, 0, h->stream>>>(bufp<double>(h, b), h->geo, side, h->nc, f, h->ctl);
+    else
+      fill_front_kernel<float><<<blocks, 256, 0, h->stream>>>(bufp<float>(h, b), h->geo, side, h->nc, f, h->ctl);
+    FAM_CUDA(h, cudaGetLastError());
   }
   return FAM_OK;
 }
@@ -227,8 +292,9 @@ static void free_fused(fam_handle* h) {
   h->fz_ready = false;
 }
 
+static bool has_front(const fam_handle* h);
 static bool use_fused(const fam_handle* h) {
-  return h->fused_oe && h->d == 2 && h->oe_type != 1 && !h->pp && h->fz_ready && h->ops.fused;
+  return h->fused_oe && h->d == 2 && h->oe_type != 1 && !h->pp && !has_front(h) && h->fz_ready && h->ops.fused;
 }
 
 static fam_status build_fused(fam_handle* h) {
@@ -284,12 +350,19 @@ static fam_status pp_prep(fam_handle* h, int b, bool want_dt) {
   return FAM_OK;
 }
 
+// Front ghosts follow the stage times: the inputs of stages 1, 2, 3 hold the
+// states at t, t + dt, t + dt/2.  The OE's input (buffer 1) keeps the front
+// rows written for stage 2's input (t + dt), which is also its own time:
+// the kernels write no images into a front side.
 static fam_status enqueue_step(fam_handle* h) {
+  if (fam_status f = fill_front(h, 0, 0.0)) return f;
   if (fam_status p = pp_prep(h, 0, true)) return p;
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
+  if (fam_status f = fill_front(h, 1, 1.0)) return f;
   if (fam_status p = pp_prep(h, 1, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   if (use_fused(h)) return enqueue_fused(h);
+  if (fam_status f = fill_front(h, 2, 0.5)) return f;
   if (fam_status p = pp_prep(h, 2, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   fam_status s = enqueue_typeI(h, 1);
@@ -315,9 +388,11 @@ static fam_status enqueue_step_profiled(fam_handle* h) {
     if (!e[q]) return fail(h, FAM_E_CUDA, "cudaEventCreate failed");
   }
   FAM_CUDA(h, cudaEventRecord(e[0], h->stream));
+  if (fam_status f = fill_front(h, 0, 0.0)) return f;
   if (fam_status p = pp_prep(h, 0, true)) return p;
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
   FAM_CUDA(h, cudaEventRecord(e[1], h->stream));
+  if (fam_status f = fill_front(h, 1, 1.0)) return f;
   if (fam_status p = pp_prep(h, 1, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   FAM_CUDA(h, cudaEventRecord(e[2], h->stream));
@@ -329,6 +404,7 @@ static fam_status enqueue_step_profiled(fam_handle* h) {
     FAM_CUDA(h, cudaEventRecord(e[4], h->stream));
     return FAM_OK;
   }
+  if (fam_status f = fill_front(h, 2, 0.5)) return f;
   if (fam_status p = pp_prep(h, 2, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   FAM_CUDA(h, cudaEventRecord(e[3], h->stream));
@@ -346,12 +422,15 @@ fam_status fam_internal_step_fixed_dt(fam_handle* h, double dt, void* const* sto
   const size_t sb = h->buf_elems * h->elem;
   FAM_CUDA(h, cudaMemcpyAsync(&h->ctl->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[0], h->buf[0], sb, cudaMemcpyDeviceToDevice, h->stream));
+  if (fam_status f = fill_front(h, 0, 0.0)) return f;
   if (fam_status p = pp_prep(h, 0, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 0, 0, 1, 1));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[1], h->buf[1], sb, cudaMemcpyDeviceToDevice, h->stream));
+  if (fam_status f = fill_front(h, 1, 1.0)) return f;
   if (fam_status p = pp_prep(h, 1, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 1, 0, 2, 2));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[2], h->buf[2], sb, cudaMemcpyDeviceToDevice, h->stream));
+  if (fam_status f = fill_front(h, 2, 0.5)) return f;
   if (fam_status p = pp_prep(h, 2, false)) return p;
   FAM_CUDA(h, h->ops.stage(h, 2, 0, 1, 3));
   if (store) FAM_CUDA(h, cudaMemcpyAsync(store[3], h->buf[1], sb, cudaMemcpyDeviceToDevice, h->stream));
@@ -371,11 +450,20 @@ static fam_status check_bc(fam_handle* h) {
   for (int dir = 0; dir < h->d; ++dir)
     if ((nb[2 * dir] == kBcPeriodic) != (nb[2 * dir + 1] == kBcPeriodic))
       return fail(h, FAM_E_INVAL, "periodic conditions come in pairs; set the opposite side too");
+  // an inflow side next to a reflective wall: their shared corner ghosts are
+  // built only where the wall's split part (fixed state) covers the corner
   if (h->d == 2)
     for (int dir = 0; dir < 2; ++dir)
-      for (int s2 = 0; s2 < 2; ++s2)
-        if (nb[2 * dir + s2] == kBcInflow && (nb[2 * (1 - dir)] == kBcReflective || nb[2 * (1 - dir) + 1] == kBcReflective))
-          return fail(h, FAM_E_UNSUPPORTED, "inflow next to a reflective wall is not built");
+      for (int s2 = 0; s2 < 2; ++s2) {
+        if (nb[2 * dir + s2] != kBcInflow) continue;
+        const int n_along_other = dir == 0 ? h->geo.nx : h->geo.ny;  // cells along the other direction's sides
+        for (int t2 = 0; t2 < 2; ++t2) {
+          const int wall = 2 * (1 - dir) + t2;
+          if (nb[wall] != kBcReflective) continue;
+          const bool covered = s2 == 0 ? h->geo.split[wall] > 0 : h->geo.split[wall] >= n_along_other;
+          if (!covered) return fail(h, FAM_E_UNSUPPORTED, "inflow next to a reflective wall is not built");
+        }
+      }
   return FAM_OK;
 }
 
@@ -742,6 +830,59 @@ fam_status fam_set_bc(fam_t h, int side, int bc, const double* inflow_state) {
   return FAM_OK;
 }
 
+// Shared tail of the side-condition setters: fixed ghosts, images, graphs.
+static fam_status side_changed(fam_handle* h) {
+  h->geo.bcx = h->geo.bc[0];
+  h->geo.bcy = h->geo.bc[2];
+  free_fused(h);
+  fam_status s = fill_inflow(h);
+  if (s) return s;
+  if (h->have_state) {
+    s = fill_ghosts(h, 0);
+    if (s) return s;
+  }
+  FAM_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->dt_valid = false;
+  return FAM_OK;
+}
+
+fam_status fam_set_bc_split(fam_t h, int side, double position, const double* state) {
+  if (!h || side < 0 || side > 3) return FAM_E_INVAL;
+  if (side >= 2 && h->d == 1) return fail(h, FAM_E_INVAL, "1D grids have only the x sides");
+  if (h->d == 1) return fail(h, FAM_E_UNSUPPORTED, "a split needs a side with more than one cell");
+  if (h->geo.bc[side] == kBcPeriodic) return fail(h, FAM_E_INVAL, "a periodic side cannot be split");
+  if (!state) return fail(h, FAM_E_INVAL, "a split needs a state");
+  // cells along the side whose centre lies below position (the same rounding
+  // as a plain evaluation of x0 + (i + 1/2) dx)
+  const bool xs = side < 2;  // the x-sides run along y
+  const int n = xs ? h->geo.ny : h->geo.nx;
+  const double lo = xs ? h->grid.y0 : h->grid.x0;
+  const double d = xs ? h->geo.dy : h->geo.dx;
+  int idx = 0;
+  while (idx < n && lo + (idx + 0.5) * d < position) ++idx;
+  h->geo.split[side] = idx;
+  for (int c = 0; c < h->nc; ++c) h->inflow[side][c] = state[c];
+  return side_changed(h);
+}
+
+fam_status fam_set_bc_front(fam_t h, int side, double a, double b, double c, const double* behind,
+                            const double* ahead) {
+  if (!h || side < 0 || side > 3) return FAM_E_INVAL;
+  if (h->d != 2 || side < 2) return fail(h, FAM_E_INVAL, "a front condition is built for the y-sides of a 2D grid");
+  if (!behind || !ahead) return fail(h, FAM_E_INVAL, "a front needs both states");
+  h->geo.bc[side] = kBcFront;
+  h->front[side][0] = a;
+  h->front[side][1] = b;
+  h->front[side][2] = c;
+  for (int q = 0; q < h->nc; ++q) {
+    h->inflow[side][q] = behind[q];
+    h->front_ahead[side][q] = ahead[q];
+  }
+  return side_changed(h);
+}
+
 fam_status fam_set_state(fam_t h, const void* U, int on_device) {
   if (!h) return FAM_E_INVAL;
   fam_status s = copy_in(h, U, on_device, 0);
@@ -894,6 +1035,7 @@ fam_status fam_residual(fam_t h, const void* U, void* R, int on_device) {
   if (fam_status b = check_bc(h)) return b;
   fam_status s = copy_in(h, U, on_device, 1);
   if (s) return s;
+  if ((s = fill_front(h, 1, 0.0))) return s;  // the state at the handle's current time
   if ((s = pp_prep(h, 1, false))) return s;
   FAM_CUDA(h, h->ops.stage(h, 1, 1, 2, 0));
   return copy_out(h, R, on_device, 2);
@@ -906,6 +1048,7 @@ fam_status fam_oe(fam_t h, double dt, const void* U, void* Uout, int on_device) 
   if (fam_status b = check_bc(h)) return b;
   fam_status s = copy_in(h, U, on_device, 1);
   if (s) return s;
+  if ((s = fill_front(h, 1, 0.0))) return s;  // the state at the handle's current time
   s = enqueue_typeI(h, 1);
   if (s) return s;
   FAM_CUDA(h, h->ops.oe(h, 1, 2, dt));

@@ -83,13 +83,19 @@ struct Geo {
   double dx, dy;
   double idx, idy;   // 1/dx, 1/dy
   // per-side conditions (x-lo, x-hi, y-lo, y-hi): 0 periodic, 1 outflow,
-  // 2 reflective wall, 3 inflow (ghosts hold a fixed state, written once)
+  // 2 reflective wall, 3 inflow (ghosts hold a fixed state, written once),
+  // 4 front (y-sides: ghosts hold one of two states by a moving straight
+  // front, rewritten before every stage and OE; no images)
   int bc[4];
   int nm;            // moments per component (planes p = c * nm + m)
   int euler;         // component 1 + dir is the normal momentum of a wall
+  // split[s] > 0: the ghost cells of side s whose nearest interior cell along
+  // the side (row for the x-sides, column for the y-sides) has index below
+  // split[s] hold the side's inflow state (no images there)
+  int split[4] = {0, 0, 0, 0};
 };
 
-enum { kBcPeriodic = 0, kBcOutflow = 1, kBcReflective = 2, kBcInflow = 3 };
+enum { kBcPeriodic = 0, kBcOutflow = 1, kBcReflective = 2, kBcInflow = 3, kBcFront = 4 };
 
 // Sign of plane (c, m) in the mirror image across a wall normal to dir: the
 // normal momentum and the moment along the normal flip (both: no flip).

@@ -59,6 +59,10 @@ struct fam_handle {
   void* buf[3] = {nullptr, nullptr, nullptr};
   FamCtl* ctl = nullptr;
   double inflow[4][4] = {{0}};   // inflow states per side (conservative averages)
+  // front side condition (y-sides, bc kBcFront): behind = inflow[side] left of
+  // x = front[0] + front[1] y + front[2] t, front_ahead right of it
+  double front[4][3] = {{0}};
+  double front_ahead[4][4] = {{0}};
   double* t1_partial = nullptr;  // Type-I OE block partial sums
   int t1_blocks = 0;
   CUtensorMap tm[3];

@@ -37,8 +37,8 @@ __device__ __forceinline__ void stage_weights(int stage, T& w0, T& w1) {
 // Padded positions (and signs) at which interior index i of one direction
 // appears: itself and its ghost images for the two sides' conditions
 // (Remark in Sec. 2.3: periodic wrap; outflow copies the boundary cell into
-// both layers; a reflective wall mirrors the first G cells; inflow ghosts are
-// fixed and get no image).
+// both layers; a reflective wall mirrors the first G cells; inflow and front
+// ghosts hold prescribed states and get no image).
 __device__ __forceinline__ int ghost_images(int i, int n, int lo, int hi, int sgn_refl, int* pos, int* sgn) {
   int q = 0;
   pos[q] = i + G; sgn[q++] = 1;
@@ -65,11 +65,14 @@ __device__ __forceinline__ void store_with_ghosts(T* __restrict__ out, const Geo
     return;
   }
   int xs[4], xsg[4], ys[4], ysg[4];
-  const int nxs = ghost_images(i, g.nx, g.bc[0], g.bc[1], reflect_sign(g, p, 0), xs, xsg);
+  // the split part of a side holds a fixed state (no images there)
+  const int bxl = j < g.split[0] ? kBcInflow : g.bc[0], bxr = j < g.split[1] ? kBcInflow : g.bc[1];
+  const int byl = i < g.split[2] ? kBcInflow : g.bc[2], byr = i < g.split[3] ? kBcInflow : g.bc[3];
+  const int nxs = ghost_images(i, g.nx, bxl, bxr, reflect_sign(g, p, 0), xs, xsg);
   int nys = 1;
   ys[0] = 0;
   ysg[0] = 1;
-  if (g.rows > 1) nys = ghost_images(j, g.ny, g.bc[2], g.bc[3], reflect_sign(g, p, 1), ys, ysg);
+  if (g.rows > 1) nys = ghost_images(j, g.ny, byl, byr, reflect_sign(g, p, 1), ys, ysg);
   T* base = out + (long long)p * g.plane;
   for (int b = 0; b < nys; ++b)
     for (int a = 0; a < nxs; ++a) base[(long long)ys[b] * g.px + xs[a]] = (xsg[a] * ysg[b] < 0) ? -v : v;

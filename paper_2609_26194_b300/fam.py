@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfam.so")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
-PERIODIC, OUTFLOW, REFLECTIVE, INFLOW = 0, 1, 2, 3
+PERIODIC, OUTFLOW, REFLECTIVE, INFLOW, FRONT = 0, 1, 2, 3, 4
 # 2D tile shapes (cells per CTA in x, y) selectable with the "tile2d" option / tune()
 TILES_2D = ((32, 8), (32, 4), (16, 8))
 STATUS = {0: "FAM_OK", 1: "FAM_E_INVAL", 2: "FAM_E_NOMEM", 3: "FAM_E_CUDA", 4: "FAM_E_NONPHYSICAL",
@@ -32,7 +32,8 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info", "fam_batch_tune",
            "fam_batch_last_error", "fam_batch_destroy", "fam_batch2d_create", "fam_batch_tile",
            "fam_step1d_noalloc", "fam_adjoint",
-           "fam_run_fixed", "fam_set_bc", "fam_tune", "fam_nonphysical_traces", "fam_batch_health")
+           "fam_run_fixed", "fam_set_bc", "fam_tune", "fam_nonphysical_traces", "fam_batch_health",
+           "fam_set_bc_split", "fam_set_bc_front")
 
 
 class FamError(RuntimeError):
@@ -73,6 +74,8 @@ def lib() -> ctypes.CDLL:
         L.fam_adjoint.argtypes = [vp, l, d, i, vp, vp, vp, i]
         L.fam_run_fixed.argtypes = [vp, l, dp]
         L.fam_set_bc.argtypes = [vp, i, i, dp]
+        L.fam_set_bc_split.argtypes = [vp, i, ctypes.c_double, dp]
+        L.fam_set_bc_front.argtypes = [vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         L.fam_tune.argtypes = [vp, d, i, ctypes.c_char_p, ctypes.POINTER(i)]
         L.fam_nonphysical_traces.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.fam_last_error.argtypes = [vp]
@@ -146,13 +149,28 @@ class Solver:
     def set_option(self, key: str, value: float):
         self._check(lib().fam_set_option(self._h, key.encode(), float(value)))
 
+    @staticmethod
+    def _state4(v):
+        arr = (ctypes.c_double * 4)(*([float(x) for x in v] + [0.0] * (4 - len(v))))
+        return ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), arr
+
     def set_bc(self, side: int, bc: int, inflow=None):
         """Per-side condition: side 0 x-low, 1 x-high, 2 y-low, 3 y-high."""
-        st = None
-        if inflow is not None:
-            arr = (ctypes.c_double * 4)(*([float(v) for v in inflow] + [0.0] * (4 - len(inflow))))
-            st = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        st, _keep = (None, None) if inflow is None else self._state4(inflow)
         self._check(lib().fam_set_bc(self._h, int(side), int(bc), st))
+
+    def set_bc_split(self, side: int, position: float, state):
+        """Ghost cells of the side whose nearest interior cell's centre along
+        the side lies below position hold state (fam_set_bc_split)."""
+        st, _keep = self._state4(state)
+        self._check(lib().fam_set_bc_split(self._h, int(side), float(position), st))
+
+    def set_bc_front(self, side: int, a: float, b: float, c: float, behind, ahead):
+        """Front condition of a y-side: behind where x < a + b y + c t, ahead
+        elsewhere (fam_set_bc_front)."""
+        pb, _kb = self._state4(behind)
+        pa, _ka = self._state4(ahead)
+        self._check(lib().fam_set_bc_front(self._h, int(side), float(a), float(b), float(c), pb, pa))
 
     def _buf(self, U):
         if _is_torch(U):

@@ -320,6 +320,35 @@ def leblanc_1d(n: int = 800, gamma: float = GAMMA) -> np.ndarray:
     return U
 
 
+# double Mach reflection (Example 4.8): states behind / ahead of the Mach 10
+# shock (rho, u, v, p) and the shock line x = a + b y + c t (through (1/6, 0)
+# at 60 degrees to the x-axis, moving at speed 10 along its normal)
+DMR_POST = (8.0, 8.25 * np.cos(np.pi / 6.0), -8.25 * np.sin(np.pi / 6.0), 116.5)
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)
+DMR_FRONT = (1.0 / 6.0, 1.0 / np.sqrt(3.0), 20.0 / np.sqrt(3.0))
+DMR_BOX = (0.0, 3.0, 0.0, 1.0)
+
+
+def double_mach_states(gamma: float = GAMMA):
+    """Conservative (behind, ahead) states of the double Mach shock."""
+    post = primitive_to_conservative_2d(*[np.array(v) for v in DMR_POST], gamma)
+    pre = primitive_to_conservative_2d(*[np.array(v) for v in DMR_PRE], gamma)
+    return tuple(float(v) for v in post), tuple(float(v) for v in pre)
+
+
+def double_mach(nx: int = 1440, ny: int = 480, gamma: float = GAMMA, nq: int = 8) -> np.ndarray:
+    """Double Mach reflection on [0, 3] x [0, 1] at t = 0: the behind state
+    left of the shock line x = 1/6 + y / sqrt(3), the ahead state right of it;
+    averages and scaled first moments by nq x nq Gauss points per cell."""
+    post, pre = double_mach_states(gamma)
+    a, b, _ = DMR_FRONT
+
+    def f(X, Y):
+        behind = X < a + b * Y
+        return np.stack([np.where(behind, post[c], pre[c]) for c in range(4)])
+    return project_2d(f, nx, ny, DMR_BOX, nq=nq)
+
+
 # smooth accuracy data (Example 4.1 and Example 4.2 of the paper)
 
 def burgers_smooth(n: int) -> np.ndarray:

@@ -176,3 +176,70 @@ def test_shu_osher_at_the_papers_cfl_runs_with_the_safeguard():
         rho = V[0, 0]
         assert np.all(rho > 0.5) and 4.0 < rho.max() < 5.0
         assert abs(rho[:40].mean() - 3.857143) < 0.05
+
+
+def _dmr_problem(nx, ny, k, pp=1):
+    post, pre = inputs.double_mach_states()
+    P = oracle.Problem(d=2, nx=nx, ny=ny, x0=0.0, x1=3.0, y0=0.0, y1=1.0, k=k, eq=oracle.EULER,
+                       bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.REFLECTIVE, oracle.FRONT), pp_limiter=pp)
+    P.inflow = (post, (0.0,) * 4, post, post)
+    P.split = (0.0, 0.0, inputs.DMR_FRONT[0], 0.0)
+    P.front = inputs.DMR_FRONT
+    P.front_ahead = pre
+    return P
+
+
+def test_split_and_front_sides_reduce_to_plain_conditions():
+    """The side conditions of Example 4.8 in their limits: a split at the
+    side's start changes nothing, a split past its end is an inflow side; a
+    front beyond the domain is an inflow side with the behind state, one
+    before it an inflow side with the ahead state; a moving front at time t
+    is the fixed front shifted by c t (no ghost centre near either line)."""
+    nx, ny = 24, 12
+    post, pre = inputs.double_mach_states()
+    U = inputs.double_mach(nx, ny)
+    base = oracle.Problem(d=2, nx=nx, ny=ny, x0=0.0, x1=3.0, y0=0.0, y1=1.0, k=5, eq=oracle.EULER,
+                          bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.OUTFLOW, oracle.OUTFLOW), pp_limiter=1)
+    base.inflow = (post, (0.0,) * 4, post, post)
+
+    def R(**kw):
+        return oracle.residual(oracle.Problem(**{**base.__dict__, **kw}), U)
+
+    r0 = R()
+    assert np.array_equal(R(split=(0.0, 0.0, 0.0, 0.0)), r0)
+    inflow_bottom = R(bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.INFLOW, oracle.OUTFLOW))
+    assert np.array_equal(R(split=(0.0, 0.0, 5.0, 0.0)), inflow_bottom)
+    inflow_top = R(bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.OUTFLOW, oracle.INFLOW))
+    front = dict(bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.OUTFLOW, oracle.FRONT), front_ahead=pre)
+    assert np.array_equal(R(front=(10.0, 0.0, 0.0), **front), inflow_top)
+    ahead_top = R(bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.OUTFLOW, oracle.INFLOW), inflow=(post, (0.0,) * 4, post, pre))
+    assert np.array_equal(R(front=(-10.0, 0.0, 0.0), **front), ahead_top)
+    # ghost centres at x = (i + 1/2) / 8: fronts at 1.3 + y / 2 (y = 1.0625, 1.1875) miss them
+    moving = R(front=(1.3 - 0.25, 0.5, 2.5), time=0.1, **front)
+    assert np.array_equal(moving, R(front=(1.3, 0.5, 0.0), **front))
+    assert not np.array_equal(moving, inflow_top)
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_double_mach_reflection_runs_with_the_safeguard(k):
+    """Example 4.8 on a coarse 60 x 20 mesh of [0, 3] x [0, 1] to T = 0.2 at
+    the guarantee's CFL: the unlimited scheme leaves the admissible set in
+    its first step; with the safeguard every step stays admissible, the gas
+    behind the incident shock near the inflow keeps the post-shock state, and
+    the reflection compresses the gas beyond the post-shock density 8."""
+    nx, ny = 60, 20
+    U = inputs.double_mach(nx, ny)
+    cfl = 1 / 6 if k <= 4 else 1 / 12
+    P0 = _dmr_problem(nx, ny, k, pp=0)
+    assert oracle.inadmissible(P0, oracle.step(P0, U, oracle.dt(P0, U, cfl)))
+    P = _dmr_problem(nx, ny, k)
+    V, t = U.copy(), 0.0
+    while t < 0.2:
+        P.time = t
+        dt = min(oracle.dt(P, V, cfl), 0.2 - t)
+        V = oracle.step(P, V, dt)
+        t += dt
+        assert oracle.inadmissible(P, V) == 0, t
+    rho = V[0, 0]
+    assert np.allclose(rho[ny // 2:, :3], 8.0, rtol=1e-3)
+    assert rho.max() > 10.0
