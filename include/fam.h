@@ -97,9 +97,12 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
  *                k <= 4, 4 for k = 5, 6) and at the volume Gauss points; the
  *                CFL rule then takes its speeds at those points, and a
  *                forward-Euler step keeps the averages admissible for CFL
- *                numbers up to 1/6 (k <= 4) or 1/12 (k = 5, 6).  The final
- *                stage and the OE then run split; no adjoint.  0 (default):
- *                off, the scheme of the paper's tests without BP/PP
+ *                numbers up to 1/6 (k <= 4) or 1/12 (k = 5, 6), stage by
+ *                stage: a step whose stage averages leave the admissible set
+ *                is discarded and retried with half the step size
+ *                (fam_rejected_steps).  The final stage and the OE then run
+ *                split; no adjoint.  0 (default): off, the scheme of the
+ *                paper's tests without BP/PP
  *   "fused_oe"   2D only: 1 runs the final RK stage and the OE in one
  *                persistent launch (not in the paper: tiles of the final
  *                stage and, once the tiles around them are done, the OE of
@@ -205,6 +208,16 @@ fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps);
  * "fused_oe", ms[2] holds the fused final stage + OE launch and ms[3] is 0;
  * *nsteps = number of profiled steps.  Synchronises the stream. */
 fam_status fam_profile(fam_t h, double* ms, long* nsteps);
+
+/* Steps discarded since the state was set (option "pp_limiter"): a step
+ * whose stage output averages leave the admissible set (rho <= 0 or p <= 0)
+ * is dropped -- the OE writes nothing, the clock and the step count stay --
+ * and retried with the step size halved, again and again (at most 30
+ * times, then FAM_E_NONPHYSICAL); an accepted step restores the CFL size.
+ * The forward-Euler bound of the safeguard holds for the speeds of each
+ * stage's input, which can exceed those of U^n the step size came from.
+ * fam_run_steps counts attempts, fam_time and fam_run accepted steps. */
+fam_status fam_rejected_steps(fam_t h, unsigned long long* count);
 
 /* Number of face quadrature points (1D: faces) at which one of the two
  * traces entering the Rusanov flux had no spectral radius, summed over every

@@ -144,6 +144,8 @@ def lib():
         L.or_dt.restype = ctypes.c_double
         L.or_oe.argtypes = [pp, ctypes.c_double, dp, dp]
         L.or_step.argtypes = [pp, dp, ctypes.c_double]
+        L.or_rejected_steps.argtypes = [ctypes.c_int]
+        L.or_rejected_steps.restype = ctypes.c_long
         L.or_run.argtypes = [pp, dp, ctypes.c_double, ctypes.c_long, ctypes.c_double, ctypes.c_int,
                              dp, ctypes.POINTER(ctypes.c_long)]
         L.or_trace_count.argtypes = []
@@ -267,6 +269,12 @@ def trace_count(reset: bool = False) -> int:
 
 def trace_reset() -> None:
     lib().or_trace_reset()
+
+
+def rejected_steps(reset: bool = False) -> int:
+    """Steps run() discarded and retried with half the step size (the
+    safeguard's stage check) since the last reset."""
+    return int(lib().or_rejected_steps(1 if reset else 0))
 
 
 def inadmissible(P: Problem, U) -> int:

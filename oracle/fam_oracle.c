@@ -522,11 +522,15 @@ static void pp_limit_cell(const or_problem* P, int ncoef, double* const* cf, dou
   if (!(ub[0] > 0.0) || !(pb > 0.0)) {
     t1 = t2 = 0.0;  /* the average itself is not admissible: keep it constant */
   } else {
-    /* targets: density min(1e-13, rho_bar) (Zhang-Shu); pressure 1e-10 p_bar,
-     * relative to the cell, since the rounding of E - |m|^2 / (2 rho) at a
-     * point scaled to a small density is about 1e-14 of E and would turn an
-     * absolute 1e-13 negative */
-    double eps = fmin(1e-13, ub[0]), epsp = 1e-10 * pb;
+    /* targets relative to the cell: density 1e-6 rho_bar, pressure 1e-8
+     * p_bar.  At a check point scaled towards vacuum the computed density
+     * carries a relative rounding error of ~1e-16 / (density target), which
+     * m^2 / (2 rho) carries into the pressure: the pressure target must stay
+     * above ~1e-16 E / (relative density target), so the two targets' product
+     * must exceed ~1e-16 E / p_bar (the absolute 1e-13 density of Zhang-Shu
+     * with 1e-10 p_bar left limited points at p < 0 in the multiscale Lax
+     * problem of Example 4.6) */
+    double eps = 1e-6 * ub[0], epsp = 1e-8 * pb;
     double u[48][4];
     double rmin = ub[0];
     for (int q = 0; q < np; ++q) {
@@ -949,7 +953,26 @@ static size_t state_len(const or_problem* P) {
   return (size_t)or_ncomp(P) * or_nmom(P) * P->nx * (P->d == 1 ? 1 : P->ny);
 }
 
-int or_step(const or_problem* P, double* U, double dt) {
+/* Averages of state V inadmissible anywhere (Euler: rho <= 0 or
+ * rho E - |m|^2 / 2 <= 0, NaN included)? */
+static int averages_inadmissible(const or_problem* P, const double* V) {
+  return P->eq == OR_EULER && or_inadmissible(P, V) > 0;
+}
+
+/* One step; with check != 0, returns 1 (U unchanged) as soon as a stage's
+ * averages leave the admissible set. */
+static int step_impl(const or_problem* P, double* U, double dt, int check);
+
+int or_step(const or_problem* P, double* U, double dt) { return step_impl(P, U, dt, 0); }
+
+static long g_rejected = 0;
+long or_rejected_steps(int reset) {
+  long v = g_rejected;
+  if (reset) g_rejected = 0;
+  return v;
+}
+
+static int step_impl(const or_problem* P, double* U, double dt, int check) {
   size_t n = state_len(P);
   double* U0 = (double*)malloc(sizeof(double) * n);
   double* Us = (double*)malloc(sizeof(double) * n);
@@ -959,17 +982,32 @@ int or_step(const or_problem* P, double* U, double dt) {
   int rc = 0;
   /* the stage states' times (they matter only to a front side condition) */
   or_problem Q = *P;
+  int bad = 0;
   /* stage 1: U1 = U0 + dt R(U0), U0 at time t */
   rc |= or_residual(&Q, U0, R);
   for (size_t q = 0; q < n; ++q) Us[q] = U0[q] + dt * R[q];
+  bad = check && averages_inadmissible(P, Us);
   /* stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt R(U1)), U1 at t + dt */
-  Q.time = P->time + dt;
-  rc |= or_residual(&Q, Us, R);
-  for (size_t q = 0; q < n; ++q) Us[q] = 0.75 * U0[q] + 0.25 * (Us[q] + dt * R[q]);
+  if (!bad) {
+    Q.time = P->time + dt;
+    rc |= or_residual(&Q, Us, R);
+    for (size_t q = 0; q < n; ++q) Us[q] = 0.75 * U0[q] + 0.25 * (Us[q] + dt * R[q]);
+    bad = check && averages_inadmissible(P, Us);
+  }
   /* stage 3: Un = 1/3 U0 + 2/3 (U2 + dt R(U2)), U2 at t + dt/2 */
-  Q.time = P->time + 0.5 * dt;
-  rc |= or_residual(&Q, Us, R);
-  for (size_t q = 0; q < n; ++q) U[q] = 1.0 / 3.0 * U0[q] + 2.0 / 3.0 * (Us[q] + dt * R[q]);
+  if (!bad) {
+    Q.time = P->time + 0.5 * dt;
+    rc |= or_residual(&Q, Us, R);
+    for (size_t q = 0; q < n; ++q) U[q] = 1.0 / 3.0 * U0[q] + 2.0 / 3.0 * (Us[q] + dt * R[q]);
+    bad = check && averages_inadmissible(P, U);
+  }
+  if (bad) {  /* discard the step: U keeps U^n */
+    memcpy(U, U0, sizeof(double) * n);
+    free(U0);
+    free(Us);
+    free(R);
+    return rc ? -1 : 1;
+  }
   /* end-of-step OE on the state at t + dt */
   Q.time = P->time + dt;
   rc |= or_oe(&Q, dt, U, NULL);
@@ -986,6 +1024,13 @@ int or_run(const or_problem* P, double* U, double T, long nsteps, double cfl, in
   long s = 0;
   int rc = 0;
   or_problem Q = *P;
+  /* With the BP/PP safeguard (Euler), a step whose stage averages leave the
+   * admissible set is discarded and retried with half the step size (the
+   * forward-Euler bound holds only for the speeds of each stage's input,
+   * which may exceed those of U^n the step size came from); r halvings so
+   * far, at most 30; an accepted step resets r. */
+  const int check = P->pp_limiter && P->eq == OR_EULER;
+  int r = 0;
   for (;;) {
     if (T > 0.0) {
       if (t >= T) break;
@@ -995,8 +1040,16 @@ int or_run(const or_problem* P, double* U, double T, long nsteps, double cfl, in
     Q.time = P->time + t;
     double dt = or_dt(&Q, U, cfl, smooth);
     if (!(dt > 0.0) || !isfinite(dt)) { rc = -1; break; }
+    dt = ldexp(dt, -r);
     if (T > 0.0 && t + dt >= T) dt = T - t;
-    if (or_step(&Q, U, dt)) { rc = -1; break; }
+    int st = step_impl(&Q, U, dt, check);
+    if (st == 1) {
+      ++g_rejected;
+      if (++r > 30) { rc = -1; break; }
+      continue;
+    }
+    if (st) { rc = -1; break; }
+    r = 0;
     t = (T > 0.0 && t + dt >= T) ? T : t + dt;
     ++s;
     for (size_t q = 0; q < n; ++q)

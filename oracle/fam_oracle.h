@@ -110,10 +110,16 @@ int or_oe(const or_problem* P, double dt, double* U, double* theta);
 
 /* One SSP-RK3 step (eq. 3 / eq. 12) followed by OE, in place. */
 int or_step(const or_problem* P, double* U, double dt);
+/* Steps or_run discarded since the last reset (the safeguard's retries with
+ * half the step size). */
+long or_rejected_steps(int reset);
 
 /* Advance to time T (last step clamped).  max_steps <= 0: unlimited.
- * nsteps_or_T: if T <= 0, runs exactly nsteps steps instead.  Returns 0 on
- * success, -1 on a non-finite value. */
+ * nsteps_or_T: if T <= 0, runs exactly nsteps accepted steps instead.  With
+ * pp_limiter (Euler), a step whose stage averages leave the admissible set is
+ * discarded and retried with the step size halved (again and again, at most
+ * 30 times; an accepted step restores the full size).  Returns 0 on success,
+ * -1 on a non-finite value or after 30 halvings. */
 int or_run(const or_problem* P, double* U, double T, long nsteps, double cfl, int smooth,
            double* t_out, long* nsteps_out);
 

@@ -244,6 +244,8 @@ static fam_status refresh_dt(fam_handle* h, double cfl, double T, bool reset_clo
   c.dye = std::pow(h->geo.dy, e);
   c.alpha_bits[0] = c.alpha_bits[1] = 0ull;
   c.blocks_done = 0;
+  c.stage_bad = 0u;
+  c.retry_exp = 0u;
   FAM_CUDA(h, cudaMemcpyAsync(h->ctl, &c, sizeof(FamCtl), cudaMemcpyHostToDevice, h->stream));
   FAM_CUDA(h, h->ops.alpha(h, 0));
   FAM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -999,6 +1001,15 @@ fam_status fam_time(fam_t h, double* t, double* dt_next, long* steps) {
   if (t) *t = c.t;
   if (dt_next) *dt_next = c.dt;
   if (steps) *steps = (long)c.step;
+  return FAM_OK;
+}
+
+fam_status fam_rejected_steps(fam_t h, unsigned long long* count) {
+  if (!h || !count) return FAM_E_INVAL;
+  FamCtl c;
+  fam_status s = ctl_read(h, &c);
+  if (s) return s;
+  *count = c.rejected;
   return FAM_OK;
 }
 

@@ -52,6 +52,15 @@ struct FamCtl {
   // where the first bounded wait that gave up was (0: none): wait kind
   // (kWait*), task or tile index, the tile waited for, mbarrier phase
   unsigned int wait_where, wait_task, wait_dep, wait_phase;
+  // BP/PP safeguard, step rejection: a stage kernel sets stage_bad when an
+  // output average leaves the admissible set; the OE then writes nothing and
+  // its epilogue discards the step (no time advance) and halves the step
+  // size: the step sizes of the retries are the CFL size times 2^-retry_exp
+  // (at most 30 halvings); an accepted step resets retry_exp.  rejected
+  // counts the discarded steps since the state was set.
+  unsigned int stage_bad;
+  unsigned int retry_exp;
+  unsigned long long rejected;
 };
 
 enum : unsigned int {
@@ -521,16 +530,29 @@ __device__ inline void step_epilogue(FamCtl* ctl, unsigned int nblocks, bool adv
   volatile unsigned long long* ab = ctl->alpha_bits;
   double ax = __longlong_as_double((long long)ab[0]);
   double ay = __longlong_as_double((long long)ab[1]);
+  // a step whose stages left the admissible set is discarded (the OE wrote
+  // nothing): the clock stays, and the retry takes half the step size
+  const bool reject = advance_time && ctl->stage_bad != 0u;
   double t = ctl->t;
-  if (advance_time && ctl->dt > 0.0) t = ctl->final_step ? ctl->T : t + ctl->dt;
+  if (advance_time && ctl->dt > 0.0 && !reject) t = ctl->final_step ? ctl->T : t + ctl->dt;
   double dt;
-  if (ctl->dim == 1)
-    dt = ctl->cfl * ctl->dxe / ax;
-  else
-    dt = ctl->cfl / (ax / ctl->dxe + ay / ctl->dye);
-  if (!(dt > 0.0) || !isfinite(dt)) {
-    dt = 0.0;
-    ctl->status |= kStatusNonFinite;
+  if (reject) {
+    ctl->stage_bad = 0u;
+    ctl->rejected += 1ull;
+    if (++ctl->retry_exp > 30u) ctl->status |= kStatusNonPhysical;
+    // the next step's safeguard kernel recomputes the size from U^n's speeds
+    dt = ctl->dt > 0.0 ? 0.5 * ctl->dt : 0.0;
+  } else {
+    if (advance_time) ctl->retry_exp = 0u;
+    if (ctl->dim == 1)
+      dt = ctl->cfl * ctl->dxe / ax;
+    else
+      dt = ctl->cfl / (ax / ctl->dxe + ay / ctl->dye);
+    if (!(dt > 0.0) || !isfinite(dt)) {
+      dt = 0.0;
+      ctl->status |= kStatusNonFinite;
+    }
+    dt = ldexp(dt, -(int)ctl->retry_exp);
   }
   if (ctl->dt_max > 0.0 && dt > ctl->dt_max) dt = ctl->dt_max;
   int fin = 0;
@@ -542,7 +564,7 @@ __device__ inline void step_epilogue(FamCtl* ctl, unsigned int nblocks, bool adv
       fin = 1;
     }
   }
-  if (advance_time && ctl->dt > 0.0) ctl->step += 1;
+  if (advance_time && ctl->dt > 0.0 && !reject) ctl->step += 1;
   ctl->t = t;
   ctl->dt = dt;
   ctl->final_step = fin;

@@ -59,7 +59,8 @@ __device__ __forceinline__ void coef1d(const T* tile, int c, int hx, T* cf) {
 template <typename T, int K, class PH, int TX, bool PP = false>
 __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const T* __restrict__ U0,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const T dt,
-                                             const int stage, const int x0, unsigned long long* ntrace) {
+                                             const int stage, const int x0, unsigned long long* ntrace,
+                                             unsigned int* stage_bad = nullptr) {
   constexpr int NC = PH::NC;
   constexpr int HX = TX + 4;
   constexpr int D = K - 1;
@@ -156,6 +157,7 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
   ph.vol_finish(VA, avg, V1);
   T w0, w1;
   stage_weights<T>(stage, w0, w1);
+  T vout[NC];  // this cell's output averages (the safeguard's stage check)
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const T fl = fL[tx * NC + c], fr = fL[(tx + 1) * NC + c];
@@ -177,9 +179,13 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
           v = w0 * u0 + w1 * (us + dt * R[m]);
         }
       }
+      if (m == 0) vout[c] = v;
       store_with_ghosts(Uout, geo, p, 0, i, v);
     }
   }
+  // BP/PP safeguard: a stage output average outside the admissible set
+  // discards the step (the OE then writes nothing; see FamCtl::stage_bad)
+  if (stage_bad != nullptr && stage != 0 && !ph.admissible(vout)) atomicOr(stage_bad, 1u);
 }
 
 
@@ -202,7 +208,8 @@ __global__ void __launch_bounds__(TX)
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;
-  stage1d_tile<T, K, PH, TX, PP>(tile, fL, fR, U0, Uout, geo, ph, T(dtd), stage, x0, &ctl->ntrace);
+  stage1d_tile<T, K, PH, TX, PP>(tile, fL, fR, U0, Uout, geo, ph, T(dtd), stage, x0, &ctl->ntrace,
+                                 PP ? &ctl->stage_bad : nullptr);
 }
 
 // OE on a staged tile (layout as for stage1d_tile); returns this thread's
@@ -293,6 +300,10 @@ __global__ void __launch_bounds__(TX)
   const bool reduce = !nonneg_bits(dt_override);
   const double dtd = reduce ? ctl->dt : dt_override;
   if (!pos_bits(dtd) && reduce) return;
+  if (reduce && ctl->stage_bad != 0u) {  // the step is discarded: U^n stays in Uout
+    if (threadIdx.x == 0) step_epilogue(ctl, gridDim.x, true);
+    return;
+  }
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;

@@ -193,7 +193,8 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const int stage,
                                              const T dt, const int x0, const int y0, const U0Src& u0src,
                                              unsigned long long* ntrace, const T idx_, const T idy_,
-                                             const T* __restrict__ theta = nullptr) {
+                                             const T* __restrict__ theta = nullptr,
+                                             unsigned int* stage_bad = nullptr) {
   constexpr int NC = PH::NC;
   using S = Smem2D<T, NC, TX, TY>;
   constexpr int HX = S::HX, HY = S::HY;
@@ -444,6 +445,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     hw[g] = T(0.5 * famgen::kGaussW[g]);
     hwx[g] = T(0.5 * famgen::kGaussW[g] * famgen::kGaussX[g]);
   }
+  T vout[NC];  // this cell's output averages (the safeguard's stage check)
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const T* fl = xL + XI(ty, tx, 0, c);
@@ -480,9 +482,13 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
           v = w0 * u0 + w1 * (us + dt * R[m]);
         }
       }
+      if (m == 0) vout[c] = v;
       store_with_ghosts(Uout, geo, p, j, i, v);
     }
   }
+  // BP/PP safeguard: a stage output average outside the admissible set
+  // discards the step (the OE then writes nothing; see FamCtl::stage_bad)
+  if (stage_bad != nullptr && stage != 0 && !ph.admissible(vout)) atomicOr(stage_bad, 1u);
 }
 
 
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   const U0FromSmem<T, TX, TY> u0src{u0s, bar + 1, ctl, want_u0};
   // (load_tile's barrier has made cst visible)
   stage2d_tile<T, K, PH, TX, TY>(tile, xL, xR, yB, yT, Uout, geo, ph, stage, cst[0], x0, y0, u0src, &ctl->ntrace,
-                                 cst[1], cst[2], theta);
+                                 cst[1], cst[2], theta, theta != nullptr ? &ctl->stage_bad : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -738,6 +744,10 @@ __global__ void __launch_bounds__(TX * TY, oe_min_blocks<T, TX * TY>())
   const bool reduce = !nonneg_bits(dt_override);
   const double dtd = reduce ? ctl->dt : dt_override;
   if (!pos_bits(dtd) && reduce) return;
+  if (reduce && ctl->stage_bad != 0u) {  // the step is discarded: U^n stays in Uout
+    if (threadIdx.x == 0) step_epilogue(ctl, gridDim.x * gridDim.y, true);
+    return;
+  }
   __shared__ T cst[2];  // dt/dx, dt/dy in T, once per block
   if (threadIdx.x == 0) {
     cst[0] = T(dtd * geo.idx);

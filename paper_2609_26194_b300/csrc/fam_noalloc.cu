@@ -31,7 +31,7 @@ namespace {
 constexpr int kMaxCells = FAM_NOALLOC_MAX_CELLS;
 constexpr int kMaxPlanes = 6;                                    // 1D Euler: 3 components x 2 moments
 constexpr long long kPitchMax = ((kMaxCells + 2 * G) + 31) / 32 * 32;  // >= any pitch used
-constexpr size_t kCtlBytes = 256;                                // FamCtl, padded to the alignment
+constexpr size_t kCtlBytes = 512;                                // FamCtl, padded to the alignment
 constexpr size_t kBufBytes = sizeof(double) * (size_t)kMaxPlanes * (size_t)kPitchMax;
 constexpr size_t kScratchBytes = kCtlBytes + 3 * kBufBytes;
 static_assert(sizeof(FamCtl) <= kCtlBytes, "control block must fit its slot");

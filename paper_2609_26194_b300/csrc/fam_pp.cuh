@@ -18,9 +18,11 @@
 // (dt/dx) a_x + (dt/dy) a_y <= w_L (1/6 or 1/12), with a the largest
 // spectral radius at the check points of the limited reconstructions: with
 // the safeguard on, the CFL rule takes its speeds there.
-// Targets: density min(1e-13, rho_bar) in FP64, 1e-4 rho_bar in FP32;
-// pressure a fraction of p_bar (1e-10 in FP64, 1e-4 in FP32), above the
-// rounding of E - |m|^2/(2 rho) at a point scaled to a small density.  The basis has P_0 = 1 and zero-mean higher
+// Targets relative to the cell: density 1e-6 rho_bar and pressure 1e-8
+// p_bar in FP64, 1e-4 of each in FP32.  At a point scaled towards vacuum the
+// computed density has a relative rounding error of ~u / (density target)
+// (u the unit roundoff), which m^2 / (2 rho) carries into the pressure, so
+// the product of the two targets must exceed ~u E / p_bar.  The basis has P_0 = 1 and zero-mean higher
 // functions, so coefficient 0 is the average and scaling the others scales
 // p - u_bar.
 #pragma once
@@ -33,14 +35,13 @@ namespace fam {
 
 template <typename T> struct PPEps;
 template <> struct PPEps<double> {
-  static __device__ __forceinline__ double rho(double rb) { return fmin(1e-13, rb); }
-  static __device__ __forceinline__ double p_frac() { return 1e-10; }
+  static __device__ __forceinline__ double rho(double rb) { return 1e-6 * rb; }
+  static __device__ __forceinline__ double p_frac() { return 1e-8; }
   // relative margin of the screen's bounds for the rounding of point values
   static __device__ __forceinline__ double tol() { return 1e-12; }
 };
-// FP32: the density target too is a fraction of the average, since
-// rho_bar + theta (rho - rho_bar) carries a rounding error of order
-// 1e-7 rho_bar, far above 1e-13
+// FP32: rho_bar + theta (rho - rho_bar) carries a rounding error of order
+// 1e-7 rho_bar
 template <> struct PPEps<float> {
   static __device__ __forceinline__ float rho(float rb) { return 1e-4f * rb; }
   static __device__ __forceinline__ float p_frac() { return 1e-4f; }

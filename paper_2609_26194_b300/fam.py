@@ -33,7 +33,7 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_batch_last_error", "fam_batch_destroy", "fam_batch2d_create", "fam_batch_tile",
            "fam_step1d_noalloc", "fam_adjoint",
            "fam_run_fixed", "fam_set_bc", "fam_tune", "fam_nonphysical_traces", "fam_batch_health",
-           "fam_set_bc_split", "fam_set_bc_front")
+           "fam_set_bc_split", "fam_set_bc_front", "fam_rejected_steps")
 
 
 class FamError(RuntimeError):
@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         L.fam_set_bc_front.argtypes = [vp, i, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         L.fam_tune.argtypes = [vp, d, i, ctypes.c_char_p, ctypes.POINTER(i)]
         L.fam_nonphysical_traces.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
+        L.fam_rejected_steps.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.fam_last_error.argtypes = [vp]
         L.fam_last_error.restype = ctypes.c_char_p
         L.fam_status_string.argtypes = [i]
@@ -238,6 +239,12 @@ class Solver:
         t, dt, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_long()
         self._check(lib().fam_time(self._h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(s)))
         return t.value, dt.value, s.value
+
+    def rejected_steps(self) -> int:
+        """Steps discarded and retried with half the step size (safeguard)."""
+        n = ctypes.c_ulonglong()
+        self._check(lib().fam_rejected_steps(self._h, ctypes.byref(n)))
+        return n.value
 
     def nonphysical_traces(self) -> int:
         """Face quadrature points whose Rusanov trace had no spectral radius,

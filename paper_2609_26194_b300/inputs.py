@@ -349,6 +349,38 @@ def double_mach(nx: int = 1440, ny: int = 480, gamma: float = GAMMA, nq: int = 8
     return project_2d(f, nx, ny, DMR_BOX, nq=nq)
 
 
+def composite_1d(n: int = 200) -> np.ndarray:
+    """A discontinuous advection profile on [-1, 1] (synthetic stand-in for
+    the composite profile of the paper's supplementary advection test): a
+    Gaussian at -0.7, a square wave on [-0.4, -0.1], a triangle on [0.1, 0.5]
+    and a parabolic bump on [0.6, 0.9].  Averages and scaled first moments by
+    8-point Gauss per cell."""
+    def f(x):
+        g = np.exp(-200.0 * (x + 0.7) ** 2)
+        sq = ((x >= -0.4) & (x < -0.1)).astype(float)
+        tri = np.clip(1.0 - np.abs(x - 0.3) / 0.2, 0.0, None)
+        bump = np.clip(1.0 - ((x - 0.75) / 0.15) ** 2, 0.0, None)
+        return (g + sq + tri + bump)[None]
+    return project_1d(f, n, -1.0, 1.0, nq=8)
+
+
+def multiscale_lax(n: int = 600, gamma: float = GAMMA) -> np.ndarray:
+    """Multiscale Lax problem of Example 4.6 on [-15, 15]: (rho, u, p) =
+    (44.5, 0.698, 352.8) on [-15, -10), (50, 0, 57.1) on [-10, 0),
+    (0.00445, 0.698, 0.03528) on [0, 10), (0.005, 0, 0.00571) on [10, 15];
+    the jumps sit on cell faces when n % 6 == 0.  Cell averages, zero
+    moments."""
+    if n % 6:
+        raise ValueError("n must be a multiple of 6 (the jumps on cell faces)")
+    x = -15.0 + (np.arange(n) + 0.5) * (30.0 / n)
+    parts = [(x < -10.0, (44.5, 0.698, 352.8)), ((x >= -10.0) & (x < 0.0), (50.0, 0.0, 57.1)),
+             ((x >= 0.0) & (x < 10.0), (0.00445, 0.698, 0.03528)), (x >= 10.0, (0.005, 0.0, 0.00571))]
+    rho, u, p = (np.select([m for m, _ in parts], [v[q] for _, v in parts]) for q in range(3))
+    U = np.zeros((3, 2, n))
+    U[:, 0] = primitive_to_conservative_1d(rho, u, p, gamma)
+    return U
+
+
 # smooth accuracy data (Example 4.1 and Example 4.2 of the paper)
 
 def burgers_smooth(n: int) -> np.ndarray:

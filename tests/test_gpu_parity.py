@@ -574,3 +574,30 @@ def test_smallest_grids(bc):
             s.sync()
             want, _, _ = oracle.run(P, U, nsteps=10, cfl=0.4)
             assert_parity(s.get_state(), want)
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_type1_oe_affine_invariance_on_the_gpu(k):
+    """The synthetic discontinuous advection profile, 200 cells on [-1, 1],
+    one period: the GPU's Type-I run on lambda u0 + c is lambda (its run on
+    u0) + c to rounding (amplified by 1 / lambda = 100), and its Type-II run on
+    the scaled data matches the oracle's within 10x the oracle's rounding
+    spread (the OE switch makes such runs sensitive, reading c21)."""
+    n, lam, c = 200, 0.01, 1.0
+    U = inputs.composite_1d(n)
+    Us = lam * U
+    Us[0, 0] += c
+    runs = {}
+    for oe in (1, 2):
+        for name, X in (("plain", U), ("scaled", Us)):
+            with fam.Solver(1, n, box=(-1.0, 1.0, 0.0, 1.0), k=k, equation=fam.ADVECTION, bc=fam.PERIODIC,
+                            gamma=1.0, oe_type=oe) as s:
+                s.set_state(X)
+                s.run(2.0, 0.2)
+                runs[oe, name] = s.get_state()
+    V, W = runs[1, "plain"], runs[1, "scaled"]
+    back = (W[0, 0] - c) / lam
+    assert np.max(np.abs(back - V[0, 0])) / np.max(np.abs(V[0, 0])) < 1e-9
+    P = oracle.Problem(d=1, nx=n, x0=-1.0, x1=1.0, k=k, eq=oracle.ADVECTION, ax=1.0, oe_type=oracle.OE_TYPE2)
+    want, spread = rounding_spread(P, Us, 0.2, T=2.0)
+    assert comp_err(runs[2, "scaled"], want) < max(1e-12, 10.0 * spread), (comp_err(runs[2, "scaled"], want), spread)

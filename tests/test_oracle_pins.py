@@ -571,3 +571,30 @@ def test_smooth_euler_2d_matches_printed_table(k, ns):
     if len(ns) == 2:
         order = np.log(errs[0] / errs[1]) / np.log(ns[1] / ns[0])
         assert abs(order - _printed_order("eu2_avg", ns[0], ns[1], k)) < 0.3
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_type1_oe_is_affine_invariant_type2_is_not(k):
+    """The supplementary advection test's point (App. "Discontinuous linear
+    advection"; App. on the Type-II reference quantity): linear advection is
+    linear, and Type-I OE takes its denominator from global statistics that
+    scale with the data, so a run on lambda u0 + c is lambda (the run on u0)
+    + c to rounding (amplified by 1 / lambda).  Type II's unnormalised local
+    sum S makes its denominator ~ 2c, which breaks the invariance.  Synthetic
+    discontinuous profile, 200 cells on [-1, 1], one period T = 2."""
+    n, lam, c = 200, 0.01, 1.0
+    U = inputs.composite_1d(n)
+    Us = lam * U
+    Us[0, 0] += c
+    out, low = {}, {}
+    for oe in (oracle.OE_TYPE1, oracle.OE_TYPE2):
+        P = oracle.Problem(d=1, nx=n, x0=-1.0, x1=1.0, k=k, eq=oracle.ADVECTION, ax=1.0, oe_type=oe)
+        V, _, _ = oracle.run(P, U, T=2.0, cfl=0.2)
+        W, _, _ = oracle.run(P, Us, T=2.0, cfl=0.2)
+        back = (W[0, 0] - c) / lam
+        out[oe] = np.max(np.abs(back - V[0, 0])) / np.max(np.abs(V[0, 0]))
+        low[oe] = back.min()
+    assert out[oracle.OE_TYPE1] < 1e-9, out
+    assert out[oracle.OE_TYPE2] > 1e-3, out
+    # the rescaled Type-II averages undershoot more near the discontinuities
+    assert low[oracle.OE_TYPE2] < low[oracle.OE_TYPE1] < 0.0, low

@@ -243,3 +243,42 @@ def test_double_mach_reflection_runs_with_the_safeguard(k):
     rho = V[0, 0]
     assert np.allclose(rho[ny // 2:, :3], 8.0, rtol=1e-3)
     assert rho.max() > 10.0
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_multiscale_lax_type1_and_type2_with_the_safeguard(k):
+    """Example 4.6 (600 cells on [-15, 15], outflow, T = 1.4) with the
+    safeguard at the guarantee's CFL: both OE types run to T with every
+    average admissible (run() retries a step whose stages leave the
+    admissible set with half its size), and the small-scale copy of the Lax
+    tube undershoots less with Type II than with Type I, as the paper
+    observes (its minimum density stays higher)."""
+    n = 600
+    U = inputs.multiscale_lax(n)
+    x = -15.0 + (np.arange(n) + 0.5) * (30.0 / n)
+    low = {}
+    for oe in (oracle.OE_TYPE1, oracle.OE_TYPE2):
+        P = oracle.Problem(d=1, nx=n, x0=-15.0, x1=15.0, k=k, eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4,
+                           pp_limiter=1, oe_type=oe)
+        V, t, _ = oracle.run(P, U, T=1.4, cfl=1 / 6 if k <= 4 else 1 / 12)
+        assert t == 1.4 and oracle.inadmissible(P, V) == 0
+        low[oe] = V[0, 0][x > 0].min()
+    assert low[oracle.OE_TYPE2] > low[oracle.OE_TYPE1] > 0.0, low
+
+
+def test_step_rejection_keeps_the_state_and_halves_the_step():
+    """The retry rule of run(): one step of k = 5 at 40x the guarantee's step
+    size leaves the admissible set on the multiscale Lax data (step() shows
+    it); run() at that CFL discards such steps and retries them with half the
+    size, so its three accepted steps end admissible, with rejections
+    counted."""
+    n = 600
+    U = inputs.multiscale_lax(n)
+    P = oracle.Problem(d=1, nx=n, x0=-15.0, x1=15.0, k=5, eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4, pp_limiter=1)
+    dt = oracle.dt(P, U, 1 / 12)
+    # a step 40x the guarantee's size breaks admissibility on this data
+    assert oracle.inadmissible(P, oracle.step(P, U, 40.0 * dt)) > 0
+    oracle.rejected_steps(reset=True)
+    V, t, st = oracle.run(P, U, nsteps=3, cfl=40.0 / 12.0)
+    assert st == 3 and oracle.inadmissible(P, V) == 0
+    assert oracle.rejected_steps() > 0
