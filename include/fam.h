@@ -49,7 +49,10 @@ typedef enum {
   FAM_E_UNSUPPORTED = 7   /* option combination not built */
 } fam_status;
 
-typedef enum { FAM_ADVECTION = 0, FAM_BURGERS = 1, FAM_EULER = 2 } fam_equation;
+/* FAM_BUCKLEY: the Buckley-Leverett equation of Example 4.3,
+ * f(u) = 4u^2 / (4u^2 + (1-u)^2), 1D only; every wave speed it uses is the
+ * bound max |f'| = 2.33203... (f' vanishes at u = 0 and 1). */
+typedef enum { FAM_ADVECTION = 0, FAM_BURGERS = 1, FAM_EULER = 2, FAM_BUCKLEY = 3 } fam_equation;
 /* Side conditions (Remark in Sec. 2.3).  fam_create takes PERIODIC or
  * OUTFLOW for every side; fam_set_bc sets any of the four per side. */
 typedef enum { FAM_BC_PERIODIC = 0, FAM_BC_OUTFLOW = 1, FAM_BC_REFLECTIVE = 2, FAM_BC_INFLOW = 3 } fam_bc;
@@ -64,12 +67,13 @@ typedef struct {
 /* Create a solver.  k in {3,4,5,6} selects FAM-k (Sec. 2.4).  gamma: ratio of
  * specific heats for FAM_EULER (the paper uses 1.4), advection speed a in
  * both directions for FAM_ADVECTION (change per direction with the options
- * "ax"/"ay"), ignored for FAM_BURGERS.  bc applies on every side (Remark in
+ * "ax"/"ay"), ignored for FAM_BURGERS and FAM_BUCKLEY.  bc applies on every side (Remark in
  * Sec. 2.3: periodic, or outflow ghost cells copying average and moments).
  * precision: 64 (FP64) or 32 (FP32).  stream: a cudaStream_t to run on, or
  * NULL for a stream the library creates.  On success *out receives the
  * handle; the state is undefined until fam_set_state().
- * Errors: FAM_E_INVAL (bad argument), FAM_E_NOMEM, FAM_E_CUDA. */
+ * Errors: FAM_E_INVAL (bad argument), FAM_E_NOMEM, FAM_E_CUDA,
+ * FAM_E_UNSUPPORTED (FAM_BUCKLEY in 2D). */
 fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int bc, double gamma,
                       int precision, void* stream);
 
@@ -87,7 +91,10 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
  *   "dt_max"     upper bound on the step size (<= 0: none)
  *   "tile2d"     2D tile shape of the stage / OE kernels: 0 = 32 x 8 (default),
  *                1 = 32 x 4, 2 = 16 x 8 cells (see fam_tune)
- *   "pp_limiter" Euler only: 1 turns on the BP/PP safeguard the paper
+ *   "pp_limiter" FAM_BUCKLEY: 1 scales each stage's reconstruction
+ *                towards the cell average until the check points below lie
+ *                in [0, 1] (the bound-preserving form for this scalar).
+ *                Euler: 1 turns on the BP/PP safeguard the paper
  *                applies after RK substeps in some tests (Sec. 2.3 remarks,
  *                Alg. 1; it cites its construction without defining it).
  *                Built as the Zhang-Shu scaling of every stage's

@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "fam_oracle.c")
 _HDR = os.path.join(_HERE, "fam_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-ADVECTION, BURGERS, EULER = 0, 1, 2
+ADVECTION, BURGERS, EULER, BUCKLEY = 0, 1, 2, 3
 PERIODIC, OUTFLOW, REFLECTIVE, INFLOW, FRONT = 0, 1, 2, 3, 4
 OE_NONE, OE_TYPE1, OE_TYPE2 = 0, 1, 2
 

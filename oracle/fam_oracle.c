@@ -200,6 +200,11 @@ static void phys_flux(const or_problem* P, int dir, const double* u, double* f) 
     f[0] = 0.5 * u[0] * u[0];
     return;
   }
+  if (P->eq == OR_BUCKLEY) {  /* Example 4.3: f = 4 u^2 / (4 u^2 + (1 - u)^2) */
+    const double a = 4.0 * u[0] * u[0], b = (1.0 - u[0]) * (1.0 - u[0]);
+    f[0] = a / (a + b);
+    return;
+  }
   double g = P->gamma;
   if (P->d == 1) {
     double rho = u[0], mom = u[1], E = u[2];
@@ -223,6 +228,13 @@ static void phys_flux(const or_problem* P, int dir, const double* u, double* f) 
 static double phys_speed(const or_problem* P, int dir, const double* u) {
   if (P->eq == OR_ADVECTION) return fabs(dir == 0 ? P->ax : P->ay);
   if (P->eq == OR_BURGERS) return fabs(u[0]);
+  /* Buckley-Leverett: f'(u) = 8 u (1 - u) / (5 u^2 - 2 u + 1)^2 vanishes at
+   * u = 0 and 1, the states of the initial data, so every speed the method
+   * takes (Rusanov, OE beta, time step) is the bound max |f'| over all u,
+   * f'(u*) with u* the root in (0, 1) of 10 u^3 - 15 u^2 + 1 = 0 (where
+   * f'' = 0; |f'| -> 0 as |u| -> infinity and is smaller at the other two
+   * roots), a Lax-Friedrichs speed */
+  if (P->eq == OR_BUCKLEY) return 2.332030375854268710378;
   double g = P->gamma;
   if (P->d == 1) {
     double rho = u[0], vel = u[1] / rho, E = u[2];
@@ -510,7 +522,45 @@ static void pp_max_speed(const or_problem* P, const double* U, double* ax, doubl
   *ay = my;
 }
 
+/* Bound-preserving scaling of a scalar reconstruction (Buckley-Leverett,
+ * whose solution stays in [0, 1]): theta = min(1, (1 - u_bar) / (M - u_bar),
+ * u_bar / (u_bar - m)) with M, m the largest and smallest value at the check
+ * points; smax (if not NULL) gets the largest |f'| at the check points of the
+ * scaled reconstruction and at the average. */
+static void bp_limit_scalar(const or_problem* P, int ncoef, double* cf, double* smax) {
+  double xi[48], eta[48];
+  int np = pp_points(1, P->k, xi, eta);
+  const double ub = cf[0];
+  double M = ub, m = ub;
+  for (int q = 0; q < np; ++q) {
+    const double v = or_eval1d(ncoef, cf, xi[q]);
+    if (v > M) M = v;
+    if (v < m) m = v;
+  }
+  double theta = 1.0;
+  if (!(ub >= 0.0 && ub <= 1.0)) theta = 0.0;
+  else {
+    if (M > 1.0) theta = fmin(theta, (1.0 - ub) / (M - ub));
+    if (m < 0.0) theta = fmin(theta, ub / (ub - m));
+  }
+  if (theta != 1.0)
+    for (int l = 1; l < ncoef; ++l) cf[l] *= theta;
+  if (smax) {
+    smax[0] = phys_speed(P, 0, &ub);
+    smax[1] = 0.0;
+    for (int q = 0; q < np; ++q) {
+      const double v = or_eval1d(ncoef, cf, xi[q]);
+      const double sq = phys_speed(P, 0, &v);
+      if (sq > smax[0]) smax[0] = sq;
+    }
+  }
+}
+
 static void pp_limit_cell(const or_problem* P, int ncoef, double* const* cf, double* smax) {
+  if (P->eq == OR_BUCKLEY) {
+    bp_limit_scalar(P, ncoef, cf[0], smax);
+    return;
+  }
   int d = P->d, nc = d + 2;
   double gm1 = P->gamma - 1.0;
   double xi[48], eta[48];
@@ -585,7 +635,7 @@ static int residual_1d(const or_problem* P, padded* A, double* R) {
 #pragma omp parallel for
   for (int i = -1; i <= nx; ++i) {
     for (int c = 0; c < nc; ++c) cell_coeffs(P, A, c, 0, i, &C[((size_t)(i + 1) * nc + c) * 6]);
-    if (P->pp_limiter && P->eq == OR_EULER) {
+    if (P->pp_limiter && (P->eq == OR_EULER || P->eq == OR_BUCKLEY)) {
       double* cf[4];
       for (int c = 0; c < nc; ++c) cf[c] = &C[((size_t)(i + 1) * nc + c) * 6];
       pp_limit_cell(P, ncoef, cf, NULL);
@@ -747,7 +797,7 @@ void or_max_speed(const or_problem* P, const double* U, double* ax, double* ay) 
 
 double or_dt(const or_problem* P, const double* U, double cfl, int smooth) {
   double ax, ay;
-  if (P->pp_limiter && P->eq == OR_EULER) pp_max_speed(P, U, &ax, &ay);
+  if (P->pp_limiter && (P->eq == OR_EULER || P->eq == OR_BUCKLEY)) pp_max_speed(P, U, &ax, &ay);
   else or_max_speed(P, U, &ax, &ay);
   double dx = (P->x1 - P->x0) / P->nx;
   double e = smooth ? P->k / 3.0 : 1.0;

@@ -25,7 +25,7 @@
 extern "C" {
 #endif
 
-enum { OR_ADVECTION = 0, OR_BURGERS = 1, OR_EULER = 2 };
+enum { OR_ADVECTION = 0, OR_BURGERS = 1, OR_EULER = 2, OR_BUCKLEY = 3 };
 enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_REFLECTIVE = 2, OR_BC_INFLOW = 3, OR_BC_FRONT = 4 };
 enum { OR_OE_NONE = 0, OR_OE_TYPE1 = 1, OR_OE_TYPE2 = 2 };
 
@@ -44,7 +44,10 @@ typedef struct {
   int oe_jump_q6;     /* 2D k=6: 1 = jumps of full Q6 (printed matrices), 0 = of p6 */
   int oe_mean;        /* Type II: 0 = S_Lambda the unnormalised sum (as printed),
                          1 = the mean over Lambda (an alternative reading) */
-  int pp_limiter;     /* Euler: 1 = scale every stage's reconstruction towards the
+  int pp_limiter;     /* Buckley-Leverett (1D): 1 = scale every stage's reconstruction
+                         towards the cell average until every check point lies in
+                         [0, 1] (the bound-preserving form for a scalar);
+                         Euler: 1 = scale every stage's reconstruction towards the
                          cell average until rho, p >= eps at the points of a
                          Gauss-Lobatto decomposition and the volume Gauss points
                          (the BP/PP safeguard the paper cites; Zhang-Shu scaling) */

@@ -524,7 +524,8 @@ fam_status fam_create(fam_t* out, const fam_grid* grid, int k, int equation, int
   *out = nullptr;
   if (grid->d != 1 && grid->d != 2) return FAM_E_INVAL;
   if (k < 3 || k > 6) return FAM_E_INVAL;
-  if (equation < FAM_ADVECTION || equation > FAM_EULER) return FAM_E_INVAL;
+  if (equation < FAM_ADVECTION || equation > FAM_BUCKLEY) return FAM_E_INVAL;
+  if (equation == FAM_BUCKLEY && grid->d != 1) return FAM_E_UNSUPPORTED;  // the paper's test is 1D
   if (bc != FAM_BC_PERIODIC && bc != FAM_BC_OUTFLOW) return FAM_E_INVAL;
   if (precision != 64 && precision != 32) return FAM_E_INVAL;
   if (grid->nx < 4 || (grid->d == 2 && grid->ny < 4)) return FAM_E_INVAL;
@@ -746,7 +747,8 @@ fam_status fam_set_option(fam_t h, const char* key, double v) {
     return select_tile(h, (int)v);
   } else if (k == "pp_limiter") {
     if (v != 0.0 && v != 1.0) return fail(h, FAM_E_INVAL, "pp_limiter must be 0 or 1");
-    if (v != 0.0 && h->eq != FAM_EULER) return fail(h, FAM_E_UNSUPPORTED, "pp_limiter is built for the Euler equations");
+    if (v != 0.0 && h->eq != FAM_EULER && h->eq != FAM_BUCKLEY)
+      return fail(h, FAM_E_UNSUPPORTED, "pp_limiter is built for the Euler and Buckley-Leverett equations");
     if (v != 0.0 && h->d == 2 && !h->theta) {
       FAM_CUDA(h, cudaStreamSynchronize(h->stream));
       if (cudaMalloc(&h->theta, 2 * (size_t)h->geo.plane * h->elem) != cudaSuccess)

@@ -25,6 +25,7 @@ bool FAM_PICK_NAME(fam_handle* h) {
     case FAM_ADVECTION: h->ops = ops_of<Impl1D<Real, K, Advection1D<Real>>>(); return true;
     case FAM_BURGERS: h->ops = ops_of<Impl1D<Real, K, Burgers1D<Real>>>(); return true;
     case FAM_EULER: h->ops = ops_of<Impl1D<Real, K, Euler1D<Real>>>(); return true;
+    case FAM_BUCKLEY: h->ops = ops_of<Impl1D<Real, K, BuckleyLeverett1D<Real>>>(); return true;
   }
 #else
 #define FAM_PICK2D(TXv, TYv)                                                                           \

@@ -119,6 +119,10 @@ template <> inline Advection1D<double> make_phys<double, Advection1D<double>>(co
 template <> inline Advection1D<float> make_phys<float, Advection1D<float>>(const fam_handle* h) { return {(float)h->ax}; }
 template <> inline Burgers1D<double> make_phys<double, Burgers1D<double>>(const fam_handle*) { return {}; }
 template <> inline Burgers1D<float> make_phys<float, Burgers1D<float>>(const fam_handle*) { return {}; }
+template <> inline BuckleyLeverett1D<double> make_phys<double, BuckleyLeverett1D<double>>(const fam_handle*) {
+  return {};
+}
+template <> inline BuckleyLeverett1D<float> make_phys<float, BuckleyLeverett1D<float>>(const fam_handle*) { return {}; }
 template <> inline Euler1D<double> make_phys<double, Euler1D<double>>(const fam_handle* h) {
   return {h->gamma, h->gamma - 1.0, 0.5 * (h->gamma - 1.0)};
 }
@@ -209,7 +213,7 @@ struct Impl1D {
     cudaError_t e = cudaFuncSetAttribute(stage1d<T, K, PH, TX1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::bytes_stage);
     if (e != cudaSuccess) return e;
-    if constexpr (PH::NC == 3) {
+    if constexpr (PH::kLimiter != 0) {
       e = cudaFuncSetAttribute(stage1d<T, K, PH, TX1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)S::bytes_stage);
       if (e != cudaSuccess) return e;
@@ -218,7 +222,7 @@ struct Impl1D {
   }
   static dim3 grid(const fam_handle* h) { return dim3((h->geo.nx + TX1 - 1) / TX1); }
   static cudaError_t stage(fam_handle* h, int in, int u0, int out, int s) {
-    if constexpr (PH::NC == 3) {
+    if constexpr (PH::kLimiter != 0) {
       if (h->pp) {
         stage1d<T, K, PH, TX1, true><<<grid(h), TX1, S::bytes_stage, h->stream>>>(
             h->tm[in], bufp<T>(h, u0), bufp<T>(h, out), h->geo, make_phys<T, PH>(h), h->ctl, s);
@@ -230,7 +234,7 @@ struct Impl1D {
     return cudaGetLastError();
   }
   static cudaError_t pp_prep(fam_handle* h, int b, bool want_dt) {
-    if constexpr (PH::NC == 3) {
+    if constexpr (PH::kLimiter != 0) {
       if (!want_dt) return cudaSuccess;  // the stage kernel scales inline
       const int blocks = std::min((h->geo.nx + 127) / 128, 148 * 8);
       pp_alpha1d<T, K, PH, 128><<<blocks, 128, 0, h->stream>>>(bufp<T>(h, b), h->geo, make_phys<T, PH>(h), h->ctl);

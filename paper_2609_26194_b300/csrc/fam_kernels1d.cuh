@@ -54,8 +54,8 @@ __device__ __forceinline__ void coef1d(const T* tile, int c, int hx, T* cf) {
 // at the instance's plane 0.  Called by all TX threads of the block.
 // ntrace (may be null) accumulates the faces of this tile at which a trace
 // has no spectral radius; each face of the grid is counted by one tile only.
-// PP (Euler only): the stage's reconstructions are scaled by the BP/PP
-// safeguard (fam_pp.cuh) before any evaluation.
+// PP (a physics with a safeguard, PH::kLimiter != 0): the stage's
+// reconstructions are scaled by it (fam_pp.cuh) before any evaluation.
 template <typename T, int K, class PH, int TX, bool PP = false>
 __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const T* __restrict__ U0,
                                              T* __restrict__ Uout, const Geo& geo, const PH& ph, const T dt,
@@ -70,12 +70,11 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
 #pragma unroll
   for (int q = 0; q < PH::NVA; ++q) VA[q] = T(0);
   T uq[NC][4];
-  if constexpr (PP && NC == 3) {
+  if constexpr (PP && PH::kLimiter != 0) {
     T cfa[NC][K];
 #pragma unroll
     for (int c = 0; c < NC; ++c) coef1d<T, K, HX>(tile, c, hx, cfa[c]);
-    T tr, tt;
-    pp_limit_1d<T, K, NC>(cfa, ph.gm1, tr, tt);
+    pp_limit_any_1d<T, K, PH>(cfa, ph);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       sym_pair<T, D, kRowInner>(cfa[c], uq[c][2], uq[c][1]);
@@ -108,12 +107,11 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
   // ring: cell x0-1 (right trace -> face 0) and cell x0+TX (left trace -> face TX)
   if (tx < 2) {
     const int rh = tx == 0 ? 1 : TX + 2;
-    if constexpr (PP && NC == 3) {
+    if constexpr (PP && PH::kLimiter != 0) {
       T cfa[NC][K];
 #pragma unroll
       for (int c = 0; c < NC; ++c) coef1d<T, K, HX>(tile, c, rh, cfa[c]);
-      T tr, tt;
-      pp_limit_1d<T, K, NC>(cfa, ph.gm1, tr, tt);
+      pp_limit_any_1d<T, K, PH>(cfa, ph);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         T r, l;
@@ -395,7 +393,7 @@ __global__ void __launch_bounds__(NT) alpha1d(const T* __restrict__ U, const Geo
   }
 }
 
-// BP/PP safeguard (Euler): the largest spectral radius at the check points of
+// Safeguard (Euler, Buckley-Leverett): the largest spectral radius at the check points of
 // every cell's limited reconstruction of U -> ctl->dt (no time advance); the
 // CFL rule of the safeguard (fam_pp.cuh).
 template <typename T, int K, class PH, int NT>
@@ -415,8 +413,7 @@ __global__ void __launch_bounds__(NT) pp_alpha1d(const T* __restrict__ U, const 
     T avg[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) avg[c] = cf[c][0];
-    T tr, tt;
-    pp_limit_1d<T, K, NC>(cf, ph.gm1, tr, tt);
+    pp_limit_any_1d<T, K, PH>(cf, ph);
     mx = max_nonneg(mx, ph.speed_x(avg));
     pp_points_1d<T, K, NC>(cf, [&](const T* u) { mx = max_nonneg(mx, ph.speed_x(u)); });
   }

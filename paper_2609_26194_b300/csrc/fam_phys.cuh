@@ -2,7 +2,7 @@
 // accumulation for the FAM stage kernels.
 //
 // Scalar laws: linear advection f = a u (Sec. 3), Burgers f = u^2/2
-// (Example 4.1).  Euler equations with ratio of specific heats gamma in
+// (Example 4.1), Buckley-Leverett f = 4u^2 / (4u^2 + (1-u)^2) (Example 4.3).  Euler equations with ratio of specific heats gamma in
 // conservative variables (Sec. 2.3): 1D (rho, rho u, E), 2D (rho, rho u,
 // rho v, E), p = (gamma - 1)(E - rho |v|^2 / 2), spectral radius of the flux
 // Jacobian |v_n| + c with c = sqrt(gamma p / rho).
@@ -21,13 +21,17 @@
 
 namespace fam {
 
-enum Equation { kAdvection = 0, kBurgers = 1, kEuler = 2 };
+enum Equation { kAdvection = 0, kBurgers = 1, kEuler = 2, kBuckley = 3 };
+
+// kLimiter: the optional safeguard a physics has (fam_pp.cuh): 0 none,
+// 1 positivity of density and pressure (Euler), 2 bounds [0, 1] (a scalar
+// whose solution stays there, Buckley-Leverett).
 
 // ----------------------------------------------------------------------------
 // 1D
 // ----------------------------------------------------------------------------
 template <typename T> struct Advection1D {
-  static constexpr int NC = 1, NVA = 1;
+  static constexpr int NC = 1, NVA = 1, kLimiter = 0;
   T a;
   __device__ __forceinline__ T flux_x(const T* u, T* f) const { f[0] = a * u[0]; return fabs(a); }
   __device__ __forceinline__ T speed_x(const T* u) const { return fabs(a); }
@@ -37,7 +41,7 @@ template <typename T> struct Advection1D {
 };
 
 template <typename T> struct Burgers1D {
-  static constexpr int NC = 1, NVA = 1;
+  static constexpr int NC = 1, NVA = 1, kLimiter = 0;
   __device__ __forceinline__ T flux_x(const T* u, T* f) const { f[0] = T(0.5) * u[0] * u[0]; return fabs(u[0]); }
   __device__ __forceinline__ T speed_x(const T* u) const { return fabs(u[0]); }
   __device__ __forceinline__ void vol_acc(const T* u, T w, T* VA) const { VA[0] = fma(w * u[0], u[0], VA[0]); }
@@ -45,8 +49,26 @@ template <typename T> struct Burgers1D {
   __device__ __forceinline__ bool admissible(const T* u) const { return true; }
 };
 
+// Buckley-Leverett (Example 4.3).  f'(u) = 8u(1-u) / (5u^2 - 2u + 1)^2
+// vanishes at u = 0 and 1, the states of the initial data, so every speed
+// (Rusanov, OE beta, time step) is the bound max |f'| over all u: f'(u*),
+// u* the root in (0, 1) of 10u^3 - 15u^2 + 1 (where f'' = 0).
+template <typename T> struct BuckleyLeverett1D {
+  static constexpr int NC = 1, NVA = 1, kLimiter = 2;
+  static __device__ __forceinline__ T flux(T u) {
+    const T a = T(4) * u * u, b = (T(1) - u) * (T(1) - u);
+    return a / (a + b);
+  }
+  static __device__ __forceinline__ T bound() { return T(2.332030375854268710378); }
+  __device__ __forceinline__ T flux_x(const T* u, T* f) const { f[0] = flux(u[0]); return bound(); }
+  __device__ __forceinline__ T speed_x(const T* u) const { return bound(); }
+  __device__ __forceinline__ void vol_acc(const T* u, T w, T* VA) const { VA[0] = fma(w, flux(u[0]), VA[0]); }
+  __device__ __forceinline__ void vol_finish(const T* VA, const T* avg, T* V1) const { V1[0] = VA[0]; }
+  __device__ __forceinline__ bool admissible(const T* u) const { return true; }
+};
+
 template <typename T> struct Euler1D {
-  static constexpr int NC = 3, NVA = 2;
+  static constexpr int NC = 3, NVA = 2, kLimiter = 1;
   T g, gm1, hgm1;  // gamma, gamma - 1, (gamma - 1)/2
   __device__ __forceinline__ T flux_x(const T* u, T* f) const {
     const T r = Fast<T>::rcp(u[0]);

@@ -245,6 +245,48 @@ __device__ __forceinline__ void pp_limit_1d(T (&cf)[NC][K], T gm1, T& th_rho, T&
   }
 }
 
+// Bound-preserving scaling of a scalar reconstruction to [0, 1]
+// (Buckley-Leverett): theta = min(1, (1 - u_bar) / (M - u_bar),
+// u_bar / (u_bar - m)), M and m the largest and smallest value at the 1D
+// check points.  A cell whose deviation bound keeps every point inside
+// [0, 1] (with the rounding margin) is left alone without its points.
+template <typename T, int K>
+__device__ __forceinline__ void bp_limit_scalar_1d(T (&cf)[1][K]) {
+  const T ub = cf[0][0];
+  const T d = pp_dev_bound_1d<T, K>(cf[0]);
+  const T tol = PPEps<T>::tol();
+  const T margin = tol * (fabs(ub) + d);
+  if (ub - d - margin >= T(0) && ub + d + margin <= T(1)) return;
+  T M = ub, m = ub;
+  pp_points_1d<T, K, 1>(cf, [&](const T* u) {
+    M = fmax(M, u[0]);
+    m = fmin(m, u[0]);
+  });
+  T th = T(1);
+  if (!(ub >= T(0) && ub <= T(1))) {
+    th = T(0);
+  } else {
+    if (M > T(1)) th = fmin(th, (T(1) - ub) / (M - ub));
+    if (m < T(0)) th = fmin(th, ub / (ub - m));
+  }
+  if (th != T(1)) {
+#pragma unroll
+    for (int l = 1; l < K; ++l) cf[0][l] *= th;
+  }
+}
+
+// The safeguard of a 1D physics on one cell's coefficients (kLimiter of
+// fam_phys.cuh: 1 positivity, 2 bounds [0, 1]).
+template <typename T, int K, class PH>
+__device__ __forceinline__ void pp_limit_any_1d(T (&cf)[PH::NC][K], const PH& ph) {
+  if constexpr (PH::kLimiter == 1) {
+    T tr, tt;
+    pp_limit_1d<T, K, PH::NC>(cf, ph.gm1, tr, tt);
+  } else if constexpr (PH::kLimiter == 2) {
+    bp_limit_scalar_1d<T, K>(cf);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 2D: check points from the coefficients of the 4 components
 // ---------------------------------------------------------------------------

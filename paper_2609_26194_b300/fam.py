@@ -17,7 +17,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfam.so")
 
-ADVECTION, BURGERS, EULER = 0, 1, 2
+ADVECTION, BURGERS, EULER, BUCKLEY = 0, 1, 2, 3
 PERIODIC, OUTFLOW, REFLECTIVE, INFLOW, FRONT = 0, 1, 2, 3, 4
 # 2D tile shapes (cells per CTA in x, y) selectable with the "tile2d" option / tune()
 TILES_2D = ((32, 8), (32, 4), (16, 8))

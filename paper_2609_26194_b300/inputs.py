@@ -381,6 +381,16 @@ def multiscale_lax(n: int = 600, gamma: float = GAMMA) -> np.ndarray:
     return U
 
 
+def buckley_leverett(n: int = 100) -> np.ndarray:
+    """Example 4.3 on [-1, 1] (periodic): u = 1 on [-0.5, 0], 0 elsewhere;
+    exact cell averages (the jumps may cut cells), zero first moments."""
+    dx = 2.0 / n
+    xl = -1.0 + np.arange(n) * dx
+    U = np.zeros((1, 2, n))
+    U[0, 0] = np.clip(np.minimum(xl + dx, 0.0) - np.maximum(xl, -0.5), 0.0, None) / dx
+    return U
+
+
 # smooth accuracy data (Example 4.1 and Example 4.2 of the paper)
 
 def burgers_smooth(n: int) -> np.ndarray:
