@@ -991,8 +991,16 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
 // theta_rho, theta; padded layout), and with want_dt the largest spectral
 // radii at the check points of the interior cells -> ctl->dt (no time
 // advance).
+// FP32 is held to 128 registers (8 blocks of 64 per SM): its common path
+// (coefficients, deviation bounds, screen) needs far fewer, and the rare
+// point passes may spill; FP64 keeps one block's worth of registers free.
+template <typename T, int NT>
+constexpr int pp_min_blocks() {
+  return sizeof(T) == 4 ? 512 / NT : 1;
+}
+
 template <typename T, int K, class PH, int NT>
-__global__ void __launch_bounds__(NT) pp_theta2d(const T* __restrict__ U, T* __restrict__ theta, const Geo geo,
+__global__ void __launch_bounds__(NT, pp_min_blocks<T, NT>()) pp_theta2d(const T* __restrict__ U, T* __restrict__ theta, const Geo geo,
                                                   const PH ph, FamCtl* __restrict__ ctl, const int want_dt) {
   constexpr int NC = PH::NC;
   constexpr int NCOEF = Recon2D<K>::NCOEF;
@@ -1007,6 +1015,7 @@ __global__ void __launch_bounds__(NT) pp_theta2d(const T* __restrict__ U, T* __r
   for (long long q0 = blockIdx.x * (long long)NT; q0 < n; q0 += (long long)gridDim.x * NT) {
     const long long q = q0 + threadIdx.x;
     double px = 0.0, py = 0.0;  // this cell's speed maxima, published for the screen of later cells
+    double seen_x = 0.0, seen_y = 0.0;  // the grid maxima this thread read
     if (q < n) {
       const int i = (int)(q % wx) - 1, j = (int)(q / wx) - 1;
       // coefficients: deviation bounds and the average here; a copy in this
@@ -1032,8 +1041,10 @@ __global__ void __launch_bounds__(NT) pp_theta2d(const T* __restrict__ U, T* __r
       const bool speeds = want_dt && interior;
       T run_x = T(0), run_y = T(0);
       if (speeds) {  // maxima reached so far (exact values of T, so the conversion is exact)
-        run_x = T(__longlong_as_double((long long)__ldcg(&ctl->alpha_bits[0])));
-        run_y = T(__longlong_as_double((long long)__ldcg(&ctl->alpha_bits[1])));
+        seen_x = __longlong_as_double((long long)__ldcg(&ctl->alpha_bits[0]));
+        seen_y = __longlong_as_double((long long)__ldcg(&ctl->alpha_bits[1]));
+        run_x = T(seen_x);
+        run_y = T(seen_y);
       }
       T tr, tt, sx = T(0), sy = T(0);
       const auto cf = [&](int c) { return SlotRef<T, NT>{cslot + c * NCOEF * NT + threadIdx.x}; };
@@ -1049,11 +1060,13 @@ __global__ void __launch_bounds__(NT) pp_theta2d(const T* __restrict__ U, T* __r
       }
     }
     if (want_dt) {
+      // publish only what raises the maxima this warp last read (after the
+      // first blocks, almost no warp does: no contention on the two words)
       px = warp_max_nonneg(px);
       py = warp_max_nonneg(py);
       if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(&ctl->alpha_bits[0], px);
-        atomic_max_nonneg(&ctl->alpha_bits[1], py);
+        if (px > seen_x) atomic_max_nonneg(&ctl->alpha_bits[0], px);
+        if (py > seen_y) atomic_max_nonneg(&ctl->alpha_bits[1], py);
       }
     }
   }
