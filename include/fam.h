@@ -188,7 +188,9 @@ fam_status fam_run(fam_t h, double T, double cfl, long max_steps, long* nsteps_o
 
 /* Enqueue nsteps steps with prescribed step sizes dts[0..nsteps-1] (host
  * array) instead of the CFL rule -- e.g. to replay a recorded step-size
- * sequence.  Asynchronous. */
+ * sequence.  Asynchronous.  With "pp_limiter", a step the safeguard rejects
+ * (fam_rejected_steps) leaves state and clock as they were and the next
+ * prescribed size follows: the rejected size is not retried. */
 fam_status fam_run_fixed(fam_t h, long nsteps, const double* dts);
 
 /* Autotuner (not in the paper): times probe_steps steps of each 2D tile
