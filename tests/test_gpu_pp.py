@@ -367,3 +367,41 @@ def test_step_rejection_matches_the_oracle():
     assert attempts == accepted + rejected
     _, spread = rounding_spread(P, U, cfl, nsteps=3)
     assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
+
+
+def test_printed_range_rectangles_full_size_sampled_step_with_safeguard():
+    """4096^2 rectangles at the shock-run ranges, k = 5, safeguard on: one
+    step of the full grid on the GPU (the unlimited scheme leaves the
+    admissible set in it).  The step size from the limited point speeds
+    equals the oracle's over the whole grid within its rounding spread; the
+    oracle recomputes sampled cells on windows (radius 10 > 3 stages x 2 +
+    OE 2) with the GPU's step size, each within 10x its window's rounding
+    spread."""
+    n, cfl = 4096, 0.55
+    U = inputs.euler2d_rectangles(n, seed=3, nrect=64)
+    s = fam.Solver(2, n, n, k=5, equation=fam.EULER, bc=fam.PERIODIC, pp_limiter=1)
+    s.set_state(U)
+    s.step(cfl)
+    s.sync()
+    dt, _, nst = s.time()
+    assert nst == 1 and s.rejected_steps() == 0
+    V = s.get_state()
+    s.close()
+    P = oracle.Problem(d=2, nx=n, ny=n, k=5, eq=oracle.EULER, pp_limiter=1)
+    want_dt = oracle.dt(P, U, cfl)
+    assert abs(dt - want_dt) <= 1e-7 * want_dt, (dt, want_dt)
+    rng = np.random.default_rng(7)
+    pts = [(0, 0), (n - 1, n - 1)] + [tuple(rng.integers(0, n, 2)) for _ in range(10)]
+    R = 10
+    dx = 1.0 / n
+    Pw = oracle.Problem(**{**P.__dict__, "nx": 2 * R + 1, "ny": 2 * R + 1, "x1": dx * (2 * R + 1),
+                           "y1": dx * (2 * R + 1)})
+    for j, i in pts:
+        jj, ii = (j + np.arange(-R, R + 1)) % n, (i + np.arange(-R, R + 1)) % n
+        W = np.ascontiguousarray(U[:, :, jj][:, :, :, ii])
+        want = oracle.step(Pw, W, dt)[:, :, R, R]
+        noisy = oracle.step(Pw, _noisy(W, j * n + i), dt)[:, :, R, R]
+        scale = np.abs(want).max(axis=1, keepdims=True) + 1e-300  # per component
+        spread = np.max(np.abs(noisy - want) / scale)
+        err = np.max(np.abs(V[:, :, j, i] - want) / scale)
+        assert err < max(1e-12, 10.0 * spread), ((j, i), err, spread)
