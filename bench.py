@@ -447,6 +447,24 @@ def batched2d_report(a, torch, prec: int = 64):
             "status": status}
 
 
+# Warp instructions per cell of one FP32 stage launch (2D Euler FAM5, 32x8
+# tiles), counted by ncu (smsp__inst_executed.sum / cells at 2048^2,
+# profiles/stage2d_k5_f32_2048.md): the FP32 stage is issue-bound, so its
+# roofline is the issue rate, one warp instruction per cycle per scheduler.
+FP32_STAGE_WARP_INST_PER_CELL = {5: 96.7}
+
+
+def _sm_clock_hz() -> float:
+    """Current SM clock of GPU 0 (NVML), else the B300's maximum 2032 MHz."""
+    try:
+        import pynvml
+        pynvml.nvmlInit()
+        h = pynvml.nvmlDeviceGetHandleByIndex(int(os.environ.get("LOCAL_RANK", "0")))
+        return float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)) * 1e6
+    except Exception:
+        return 2032e6
+
+
 def _hbm_peak() -> float:
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -527,8 +545,23 @@ def configs_report(a, torch):
     s.run_steps(steps, 0.55)
     s.set_state(U32)
     sec = timed(s, st, lambda: s.run_steps(steps, 0.55))
+    s.set_option("profile", 1)
+    s.set_state(U32)
+    for _ in range(2):
+        s.step(0.55)
+    prof, pst = s.profile()
+    stage_ms = sum(prof[:3]) / (3 * max(1, pst))
+    clk = _sm_clock_hz()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    issue_peak = sms * 4 * clk  # warp instructions per second
+    achieved = FP32_STAGE_WARP_INST_PER_CELL[5] * n * n / (stage_ms * 1e-3) if tile == (32, 8) else None
     out["euler2d_smooth_4096_k5_f32"] = {"value": 3.0 * n * n * steps / sec, "seconds": sec, "steps": steps,
-                                         "tile": list(tile)}
+                                         "tile": list(tile), "stage_ms": stage_ms,
+                                         "issue_roofline": {"bound": "issue", "unit": "warp instructions/s",
+                                                            "achieved": achieved, "peak": issue_peak,
+                                                            "frac": achieved / issue_peak if achieved else None,
+                                                            "instructions_per_cell": FP32_STAGE_WARP_INST_PER_CELL[5],
+                                                            "source": "ncu count at 32x8 tiles; SM clock from NVML"}}
     s.close()
     # the bench workload (FP64, k = 5) with the BP/PP safeguard on: what the
     # per-stage scaling-factor kernel costs where it changes nothing
@@ -601,6 +634,7 @@ def printed_rectangles_report(torch, n: int = 4096, max_steps: int = 20):
             status = str(e)
         t, _, nst = s.time()
         out[f"k{k}_f{prec}_safeguard"] = {"status": status, "steps": nst, "t": t,
+                                           "rejected_steps": s.rejected_steps(),
                                            "nonphysical_traces": s.nonphysical_traces(),
                                            "value": 3.0 * n * n * max_steps / sec, "unit": UNIT, "seconds": sec}
         s.close()
@@ -635,6 +669,7 @@ def extreme_1d_report(torch):
             sec = time.perf_counter() - t0
             t, _, _ = s.time()
             out[f"{name}_k{k}"] = {"cells": n, "cfl": cfl, "T": T, "t": t, "steps": nst, "status": status,
+                                   "rejected_steps": s.rejected_steps(),
                                    "seconds": sec, "value": 3.0 * n * nst / sec, "unit": UNIT}
             s.close()
     return out
@@ -679,6 +714,7 @@ def double_mach_report(torch, nx: int = 1440, ny: int = 480):
     sec = time.perf_counter() - t0
     rho = s.get_state()[0, 0]
     out["f32_complete_run"] = {"status": status, "steps": nst, "seconds": sec,
+                               "rejected_steps": s.rejected_steps(),
                                "value": 3.0 * nx * ny * nst / sec, "unit": UNIT,
                                "rho_max": float(rho.max()), "rho_min": float(rho.min())}
     s.close()
