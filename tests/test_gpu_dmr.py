@@ -129,3 +129,19 @@ def test_fp32_run_stays_admissible():
     s.close()
     assert abs(t - 0.2) < 1e-12
     assert got[0, 0].min() > 1.0 and got[0, 0].max() > 10.0
+
+
+def test_side_condition_errors():
+    s = fam.Solver(2, 32, 16, k=5, equation=fam.EULER, bc=fam.PERIODIC)
+    with pytest.raises(fam.FamError) as e:
+        s.set_bc_split(2, 0.5, POST)  # a periodic side cannot be split
+    assert e.value.code == 1
+    with pytest.raises(fam.FamError) as e:
+        s.set_bc_front(0, 0.1, 0.0, 0.0, POST, PRE)  # fronts are built for the y-sides
+    assert e.value.code == 1
+    s.close()
+    s = fam.Solver(1, 64, k=5, equation=fam.EULER, bc=fam.OUTFLOW)
+    with pytest.raises(fam.FamError) as e:
+        s.set_bc_split(0, 0.5, POST[:3])
+    assert e.value.code == 7
+    s.close()

@@ -405,3 +405,31 @@ def test_printed_range_rectangles_full_size_sampled_step_with_safeguard():
         spread = np.max(np.abs(noisy - want) / scale)
         err = np.max(np.abs(V[:, :, j, i] - want) / scale)
         assert err < max(1e-12, 10.0 * spread), ((j, i), err, spread)
+
+
+def test_step_rejection_2d_matches_the_oracle():
+    """The printed-range rectangles (48 x 40, k = 5) at 1000x the guarantee's
+    step size (their near-vacuum check points keep the size small, so a
+    smaller factor breaks nothing): the 2D stage kernels flag output averages
+    outside the admissible set and the OE discards the step; single attempts
+    until 3 steps are accepted: the rejected count equals the oracle run()'s,
+    and the state its result within 10x its rounding spread."""
+    U = _rect(48, 40)
+    cfl = 1000.0 / 12.0
+    s, P = make(2, (48, 40), 5, "euler", "periodic", pp_limiter=1)
+    P.pp_limiter = 1
+    s.set_state(U)
+    attempts = 0
+    while s.time()[2] < 3 and attempts < 200:
+        s.step(cfl)
+        s.sync()
+        attempts += 1
+    rejected = s.rejected_steps()
+    got = s.get_state()
+    s.close()
+    oracle.rejected_steps(reset=True)
+    want, _, st = oracle.run(P, U, nsteps=3, cfl=cfl)
+    assert st == 3 and rejected == oracle.rejected_steps() and rejected > 0
+    assert attempts == 3 + rejected
+    _, spread = rounding_spread(P, U, cfl, nsteps=3)
+    assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
