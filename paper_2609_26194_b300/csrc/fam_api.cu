@@ -452,6 +452,9 @@ static fam_status check_bc(fam_handle* h) {
   for (int dir = 0; dir < h->d; ++dir)
     if ((nb[2 * dir] == kBcPeriodic) != (nb[2 * dir + 1] == kBcPeriodic))
       return fail(h, FAM_E_INVAL, "periodic conditions come in pairs; set the opposite side too");
+  for (int side = 0; side < 4; ++side)
+    if (h->geo.split[side] > 0 && nb[side] == kBcPeriodic)
+      return fail(h, FAM_E_INVAL, "a periodic side cannot be split");
   // an inflow side next to a reflective wall: their shared corner ghosts are
   // built only where the wall's split part (fixed state) covers the corner
   if (h->d == 2)

@@ -145,3 +145,13 @@ def test_side_condition_errors():
         s.set_bc_split(0, 0.5, POST[:3])
     assert e.value.code == 7
     s.close()
+    # a split side turned periodic afterwards is refused when a step uses it
+    s = fam.Solver(2, 32, 16, k=5, equation=fam.EULER, bc=fam.OUTFLOW)
+    s.set_bc_split(2, 0.5, POST)
+    s.set_bc(2, fam.PERIODIC)
+    s.set_bc(3, fam.PERIODIC)
+    s.set_state(inputs.double_mach(32, 16))
+    with pytest.raises(fam.FamError) as e:
+        s.step(0.1)
+    assert e.value.code == 1
+    s.close()
