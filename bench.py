@@ -367,10 +367,14 @@ def batched_printed_ranges(a, nx, ks):
         sec = time.perf_counter() - t0
         ntr, _, bad = b.health()
         _, _, steps = b.times()
+        rej = b.rejected_steps()
         b.close()
+        # rejected attempts are not counted as work
         cs = 3.0 * float(np.sum(np.asarray(nx) * steps))
         out[f"safeguard_cfl_{cfl:.4g}"] = {"status": status, "completed": int(np.sum(bad == 0)),
                                            "stopped": int(np.sum(bad > 0)), "nonphysical_traces": int(np.sum(ntr)),
+                                           "rejected_steps": int(np.sum(rej)),
+                                           "instances_with_rejections": int(np.sum(rej > 0)),
                                            "value": cs / sec, "unit": UNIT, "seconds": sec}
     return out
 

@@ -304,7 +304,8 @@ fam_status fam_batch2d_create(fam_batch_t* out, int n_inst, const int* nx, const
  * "tile_x" (1D: 64 / 128 / 256 cells per tile), "tile2d" (2D: 0 / 1 / 2 for
  * 32x8 / 32x4 / 16x8 cells per tile), "blocks_per_sm" (<= 0: the occupancy
  * maximum), "pp_limiter" (1D Euler: the BP/PP safeguard of fam_set_option,
- * in every instance), "wait_limit_ns" (how long a block waits at the persistent
+ * in every instance, step rejection included: each instance discards and
+ * retries its own steps, fam_batch_rejected_steps), "wait_limit_ns" (how long a block waits at the persistent
  * kernel's grid barrier before the launch gives up with FAM_E_TIMEOUT from
  * fam_batch_sync; 0 restores the default of 2 s; at most 60 s),
  * "test_barrier_extra" (test hook, 0 or 1: the grid barrier waits for one
@@ -320,6 +321,10 @@ fam_status fam_batch_get_state(fam_batch_t h, void* U, int on_device);
 /* Advance every instance by nsteps steps (eq. 3/12 + OE) in ONE cooperative
  * persistent kernel launch (a tile work list walked pass by pass with
  * bounded grid barriers), captured in a CUDA graph per (nsteps, cfl).
+ * With "pp_limiter", nsteps counts attempts: an instance whose attempt the
+ * safeguard rejects keeps its state and clock and takes its next attempt
+ * with half the step size, so it advances by fewer accepted steps
+ * (fam_batch_times) than the others.
  * Asynchronous; fam_batch_sync() waits and reports device flags. */
 fam_status fam_batch_run(fam_batch_t h, long nsteps, double cfl);
 fam_status fam_batch_sync(fam_batch_t h);
@@ -334,6 +339,15 @@ fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps);
  * that step's output) while the other instances go on; fam_batch_sync then
  * reports FAM_E_NONPHYSICAL for the batch.  Synchronous. */
 fam_status fam_batch_health(fam_batch_t h, unsigned long long* ntrace, int* status, long* bad_step);
+/* Per-instance attempts discarded since the state was set (option
+ * "pp_limiter"; array of n_inst): an attempt whose stage output averages
+ * leave the admissible set (rho <= 0 or p <= 0) writes nothing -- the
+ * instance's later stages and OE skip it, its clock and step count stay --
+ * and the instance's next attempt takes half the step size, again and again
+ * (at most 30 halvings; the 31st stops the instance with FAM_E_NONPHYSICAL,
+ * bad_step = the step it could not take); an accepted step restores the CFL
+ * size.  The same rule as fam_rejected_steps, per instance.  Synchronous. */
+fam_status fam_batch_rejected_steps(fam_batch_t h, unsigned long long* count);
 /* Launch shape: tile width (2D: the tile's x extent), blocks of the
  * persistent grid, tiles, cells. */
 fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, long* cells);

@@ -158,6 +158,14 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
         const BatchInst I = inst[td.x];
         const double dtd = ictl[td.x].dt;
         if (!(dtd > 0.0)) continue;
+        if constexpr (PP) {
+          // a stage that left the admissible set discards the instance's
+          // step: its later stages and its OE skip it (A keeps U^n).  Only
+          // the bits of earlier passes are read, which the grid barrier has
+          // settled, so every thread of the block takes the same branch.
+          const unsigned int bad = *reinterpret_cast<volatile const unsigned int*>(&ictl[td.x].stage_bad);
+          if ((bad & ((1u << pass) - 1u)) != 0u) continue;
+        }
         __syncthreads();
         load_tile_plain<T, TX>(tile, in, I, NP, td.y);
         __syncthreads();
@@ -169,11 +177,12 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
           const T* U0 = A + I.off;
           T* Uo = out + I.off;
           unsigned long long* nt = &ictl[td.x].ntrace;
+          unsigned int* sb = PP ? &ictl[td.x].stage_bad : nullptr;
           switch (I.k) {
-            case 3: stage1d_tile<T, 3, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
-            case 4: stage1d_tile<T, 4, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
-            case 5: stage1d_tile<T, 5, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
-            default: stage1d_tile<T, 6, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt); break;
+            case 3: stage1d_tile<T, 3, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt, sb); break;
+            case 4: stage1d_tile<T, 4, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt, sb); break;
+            case 5: stage1d_tile<T, 5, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt, sb); break;
+            default: stage1d_tile<T, 6, PH, TX, PP>(tile, fL, fR, U0, Uo, geo, ph, dt, pass, td.y, nt, sb); break;
           }
         } else {
           T* tr = faces;
@@ -201,12 +210,25 @@ __global__ void __launch_bounds__(TX) batched1d_run(const BatchInst* __restrict_
     for (int i = blockIdx.x * TX + threadIdx.x; i < ninst; i += nb * TX) {
       BatchCtl c = ictl[i];
       if (c.dt > 0.0) {
-        c.t += c.dt;
-        c.steps += 1;
-        const double a = __longlong_as_double((long long)c.alpha_bits);
-        double dt = cfl * inst[i].dx / a;
-        if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; c.status |= kStatusNonFinite; }
-        c.dt = dt;
+        if (PP && c.stage_bad != 0u) {
+          // discarded step: the clock stays and the retry takes half the
+          // size (U^n's speeds are those the discarded size came from)
+          c.stage_bad = 0u;
+          c.rejected += 1ull;
+          if (++c.retry_exp > 30u) {  // the step that could not be taken stops the instance
+            c.status |= kStatusNonPhysical;
+            if (c.bad_step == 0ull) c.bad_step = c.steps + 1ull;
+          }
+          c.dt = 0.5 * c.dt;
+        } else {
+          c.t += c.dt;
+          c.steps += 1;
+          c.retry_exp = 0u;
+          const double a = __longlong_as_double((long long)c.alpha_bits);
+          double dt = cfl * inst[i].dx / a;
+          if (!(dt > 0.0) || !isfinite(dt)) { dt = 0.0; c.status |= kStatusNonFinite; }
+          c.dt = dt;
+        }
         close_instance_step(c, &g->status);
       }
       c.alpha_bits = 0ull;
@@ -744,6 +766,15 @@ fam_status fam_batch_times(fam_batch_t h, double* t, double* dt, long* steps) {
     if (dt) dt[i] = c[i].dt;
     if (steps) steps[i] = (long)c[i].steps;
   }
+  return FAM_OK;
+}
+
+fam_status fam_batch_rejected_steps(fam_batch_t h, unsigned long long* count) {
+  if (!h || !count) return FAM_E_INVAL;
+  std::vector<BatchCtl> c(h->n);
+  FAMB_CUDA(h, cudaMemcpyAsync(c.data(), h->ictl, sizeof(BatchCtl) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->n; ++i) count[i] = c[i].rejected;
   return FAM_OK;
 }
 

@@ -22,14 +22,21 @@ struct BatchInst {
 // (x and y, as bit patterns of non-negative doubles), steps taken; the
 // instance's own health: face points whose trace had no spectral radius,
 // status bits, and the step whose output was first flagged (0: none; the
-// instance stops after that step while the others go on).
+// instance stops after that step while the others go on).  BP/PP safeguard
+// (1D Euler), step rejection: the stage tiles set bit s of stage_bad when a
+// cell average of stage s leaves the admissible set; the instance's later
+// stages and its OE then skip the step (A keeps U^n) and the clock pass
+// discards it, halves the step size (retry_exp halvings so far, at most 30)
+// and counts it in rejected.
 struct BatchCtl {
   double dt, t;
   unsigned long long alpha_bits, alpha_bits_y;
   unsigned long long steps;
   unsigned long long ntrace;
-  unsigned int status, pad;
+  unsigned int status, stage_bad;
   unsigned long long bad_step;
+  unsigned int retry_exp, pad;
+  unsigned long long rejected;
 };
 
 // End of an instance's step in the clock pass: a flagged instance records

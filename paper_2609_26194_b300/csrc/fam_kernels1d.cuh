@@ -182,8 +182,9 @@ __device__ __forceinline__ void stage1d_tile(const T* tile, T* fL, T* fR, const 
     }
   }
   // BP/PP safeguard: a stage output average outside the admissible set
-  // discards the step (the OE then writes nothing; see FamCtl::stage_bad)
-  if (stage_bad != nullptr && stage != 0 && !ph.admissible(vout)) atomicOr(stage_bad, 1u);
+  // discards the step (the OE then writes nothing; see FamCtl::stage_bad);
+  // bit `stage` records which stage it was
+  if (stage_bad != nullptr && stage != 0 && !ph.admissible(vout)) atomicOr(stage_bad, 1u << stage);
 }
 
 
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(TX)
 
   const double dtd = (stage == 0) ? 0.0 : ctl->dt;
   if (stage != 0 && !pos_bits(dtd)) return;
+  if (PP && stage >= 2 && ctl->stage_bad != 0u) return;  // an earlier stage discarded the step
   const int x0 = blockIdx.x * TX;
   if (threadIdx.x == 0) prefetch_tmap(&tm_in);
   if (!load_tile_1d<T, NP, HX>(tile, bar, &tm_in, x0, ctl)) return;

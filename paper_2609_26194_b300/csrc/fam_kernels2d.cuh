@@ -488,7 +488,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   }
   // BP/PP safeguard: a stage output average outside the admissible set
   // discards the step (the OE then writes nothing; see FamCtl::stage_bad)
-  if (stage_bad != nullptr && stage != 0 && !ph.admissible(vout)) atomicOr(stage_bad, 1u);
+  if (stage_bad != nullptr && stage != 0 && !ph.admissible(vout)) atomicOr(stage_bad, 1u << stage);
 }
 
 
@@ -524,6 +524,8 @@ __global__ void __launch_bounds__(TX * TY, stage_min_blocks<T, TX * TY>())
   __shared__ T cst[3];
   const double dtd = (stage == 0) ? 0.0 : ctl->dt;
   if (stage != 0 && !pos_bits(dtd)) return;  // run finished: keep the state
+  // BP/PP safeguard: an earlier stage discarded the step
+  if (theta != nullptr && stage >= 2 && ctl->stage_bad != 0u) return;
   if (threadIdx.x == 0) {
     cst[0] = T(dtd);
     cst[1] = T(geo.idx);

@@ -33,7 +33,7 @@ EXPORTS = ("fam_create", "fam_set_option", "fam_set_state", "fam_get_state", "fa
            "fam_batch_last_error", "fam_batch_destroy", "fam_batch2d_create", "fam_batch_tile",
            "fam_step1d_noalloc", "fam_adjoint",
            "fam_run_fixed", "fam_set_bc", "fam_tune", "fam_nonphysical_traces", "fam_batch_health",
-           "fam_set_bc_split", "fam_set_bc_front", "fam_rejected_steps")
+           "fam_set_bc_split", "fam_set_bc_front", "fam_rejected_steps", "fam_batch_rejected_steps")
 
 
 class FamError(RuntimeError):
@@ -429,6 +429,13 @@ class Batch:
         return (np.array(nt[:], dtype=np.int64), np.array(st[:], dtype=np.int32),
                 np.array(bs[:], dtype=np.int64))
 
+    def rejected_steps(self) -> np.ndarray:
+        """Per instance: attempts the BP/PP safeguard discarded (each retried
+        with half the step size) since the state was set."""
+        c = (ctypes.c_ulonglong * self.n)()
+        self._check(lib().fam_batch_rejected_steps(self._h, c))
+        return np.array(c[:], dtype=np.int64)
+
     def info(self) -> dict:
         tx, g, nt, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_long(), ctypes.c_long()
         self._check(lib().fam_batch_info(self._h, ctypes.byref(tx), ctypes.byref(g), ctypes.byref(nt),
@@ -466,13 +473,14 @@ def _batch_sigs(L):
     L.fam_batch_info.argtypes = [vp, ip, ip, ctypes.POINTER(l), ctypes.POINTER(l)]
     L.fam_batch_tune.argtypes = [vp, d, i, ctypes.c_char_p, ip, ip]
     L.fam_batch_health.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), ip, ctypes.POINTER(l)]
+    L.fam_batch_rejected_steps.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
     L.fam_batch_last_error.argtypes = [vp]
     L.fam_batch_last_error.restype = ctypes.c_char_p
     L.fam_batch_destroy.argtypes = [vp]
     L.fam_batch_destroy.restype = None
     for name in ("fam_batch_create", "fam_batch2d_create", "fam_batch_set_option", "fam_batch_set_state",
                  "fam_batch_get_state", "fam_batch_run", "fam_batch_sync", "fam_batch_times", "fam_batch_info",
-                 "fam_batch_tune", "fam_batch_tile", "fam_batch_health"):
+                 "fam_batch_tune", "fam_batch_tile", "fam_batch_health", "fam_batch_rejected_steps"):
         getattr(L, name).restype = ctypes.c_int
     _batch_ready = True
 

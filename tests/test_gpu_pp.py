@@ -369,6 +369,60 @@ def test_step_rejection_matches_the_oracle():
     assert comp_err(got, want) < max(1e-12, 10.0 * spread), (comp_err(got, want), spread)
 
 
+def test_batch_step_rejection_matches_single_runs_and_the_oracle():
+    """The first 80 printed-range Riemann instances of at most 300 cells,
+    safeguard on, 40 attempts at CFL 1/2 (6x the guarantee's size for k = 5,
+    6): each instance discards and retries its own steps, so the batch
+    equals every instance's single-problem run of 40 attempts bit for bit
+    (state, time, accepted and rejected counts).  Against the oracle: the
+    state equals its run to the same number of accepted steps within 10x its
+    rounding spread, and the batch's rejected count r lies between the
+    oracle's count at those steps and at one step more (attempts after the
+    last accepted one are all rejected)."""
+    rng = np.random.default_rng(4)
+    ns = np.rint(np.exp(rng.uniform(np.log(64), np.log(16384), 4096))).astype(int)
+    ks = rng.integers(3, 7, 4096)
+    pick = [i for i in range(4096) if ns[i] <= 300][:80]
+    nx = [int(ns[i]) for i in pick]
+    kk = [int(ks[i]) for i in pick]
+    states = [inputs.euler1d_riemann(n, seed=4 + i, **PRINTED_1D) for n, i in zip(nx, pick)]
+    cfl, attempts = 0.5, 40
+    b = fam.Batch(nx, kk, bc=fam.OUTFLOW)
+    b.set_option("pp_limiter", 1)
+    b.set_state(states)
+    b.run(attempts, cfl)
+    b.sync()
+    got = b.get_state()
+    t, dt, steps = b.times()
+    rej = b.rejected_steps()
+    _, status, _ = b.health()
+    b.close()
+    assert np.all(status == 0)
+    assert np.all(steps + rej == attempts)
+    assert np.sum(rej > 0) >= 10, rej
+    for q in range(len(pick)):
+        if rej[q] == 0 and q % 8:
+            continue  # every rejecting instance, and every 8th one
+        with fam.Solver(1, nx[q], k=kk[q], equation=fam.EULER, bc=fam.OUTFLOW, pp_limiter=1) as s:
+            s.set_state(states[q])
+            s.run_steps(attempts, cfl)
+            s.sync()
+            assert np.array_equal(got[q], s.get_state()), q
+            t1, _, st1 = s.time()
+            assert (t1, st1) == (t[q], steps[q]), q
+            assert s.rejected_steps() == rej[q], q
+        P = oracle.Problem(d=1, nx=nx[q], k=kk[q], eq=oracle.EULER, bc=(oracle.OUTFLOW,) * 4, pp_limiter=1)
+        oracle.rejected_steps(reset=True)
+        want, t_or, st = oracle.run(P, states[q], nsteps=int(steps[q]), cfl=cfl)
+        r_at = oracle.rejected_steps(reset=True)
+        oracle.run(P, states[q], nsteps=int(steps[q]) + 1, cfl=cfl)
+        r_next = oracle.rejected_steps(reset=True)
+        assert st == steps[q] and r_at <= rej[q] <= r_next, (q, r_at, rej[q], r_next)
+        assert abs(t_or - t[q]) <= 1e-9 * t_or, q
+        _, spread = rounding_spread(P, states[q], cfl, nsteps=int(steps[q]))
+        assert comp_err(got[q], want) < max(1e-12, 10.0 * spread), (q, comp_err(got[q], want), spread)
+
+
 def test_printed_range_rectangles_full_size_sampled_step_with_safeguard():
     """4096^2 rectangles at the shock-run ranges, k = 5, safeguard on: one
     step of the full grid on the GPU (the unlimited scheme leaves the
