@@ -372,56 +372,51 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   __syncthreads();
 
   // ---- phase B: Rusanov fluxes at every face Gauss point -----------------
-  // face point it: x-faces first (it = g * NFX + face), then y-faces
-  constexpr int NXP = NFX * 4, NYP = NFY * 4;
+  // Each thread takes the x-face slot and the y-face slot of its own index
+  // (slots 0 .. TX*TY - 1 of each family) at the four Gauss points, with
+  // compile-time offsets; the last column of x-faces and the last row of
+  // y-faces (slots TX*TY ..) follow, one point per thread.
   unsigned nbad = 0;  // owned face points with a trace that has no spectral radius
-  for (int it = threadIdx.x; it < NXP + NYP; it += NT) {
+  // twice the Rusanov flux, f^- + f^+ - alpha (u^+ - u^-), into the slot's
+  // left-side entry (the factor 1/2 is folded into the quadrature weights of
+  // phase C, exact: a power of 2); true if a trace has no spectral radius
+  auto face_point = [&](T* slot, const T* other, const int cs, const bool xdir) -> bool {
     T uL[NC], uR[NC], fL[NC], fR[NC];
-    T* slot;
-    const T* other;
-    int cs;  // component stride
-    T sL, sR;
-    if (it < NXP) {
-      const int g = it / NFX, f = it - g * NFX;
-      slot = xL + g * NC * NFX + f;
-      other = xR + g * NC * NFX + f;
-      cs = NFX;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) { uL[c] = slot[c * NFX]; uR[c] = other[c * NFX]; }
-      sL = ph.flux_x(uL, fL);
-      sR = ph.flux_x(uR, fR);
-    } else {
-      const int q = it - NXP, g = q / NFY, f = q - g * NFY;
-      slot = yB + g * NC * NFY + f;
-      other = yT + g * NC * NFY + f;
-      cs = NFY;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) { uL[c] = slot[c * NFY]; uR[c] = other[c * NFY]; }
-      sL = ph.flux_y(uL, fL);
-      sR = ph.flux_y(uR, fR);
-    }
-    // twice the Rusanov flux, f^- + f^+ - alpha (u^+ - u^-); the factor 1/2
-    // is folded into the quadrature weights of phase C (exact: a power of 2)
+    for (int c = 0; c < NC; ++c) { uL[c] = slot[c * cs]; uR[c] = other[c * cs]; }
+    const T sL = xdir ? ph.flux_x(uL, fL) : ph.flux_y(uL, fL);
+    const T sR = xdir ? ph.flux_x(uR, fR) : ph.flux_y(uR, fR);
     const T a = rusanov_speed(sL, sR);
 #pragma unroll
     for (int c = 0; c < NC; ++c) slot[c * cs] = fma(-a, uR[c] - uL[c], fL[c] + fR[c]);
-    if (nan_bits(sL) || nan_bits(sR)) {
-      // the face's owner: the tile holding the cell to its right (top), or
-      // for the grid's last face the tile to its left (bottom)
-      bool own;
-      if (it < NXP) {
-        const int f = it - (it / NFX) * NFX;
-        const int row = f < TX * TY ? f / TX : f - TX * TY;
-        const int col = f < TX * TY ? ((f % TX) - row) & (TX - 1) : TX;
-        const int F = x0 + col;
-        own = y0 + row < geo.ny && F <= geo.nx && (col < TX || F == geo.nx);
-      } else {
-        const int q = it - NXP, f = q - (q / NFY) * NFY;
-        const int row = f / TX, col = f % TX;
-        const int F = y0 + row;
-        own = x0 + col < geo.nx && F <= geo.ny && (row < TY || F == geo.ny);
-      }
-      nbad += own ? 1u : 0u;
+    return nan_bits(sL) || nan_bits(sR);
+  };
+  {
+    // the face's owner: the tile holding the cell to its right (top), or for
+    // the grid's last face the tile to its left (bottom).  x-face slot
+    // threadIdx.x is row ty, column (tx - ty) mod TX; y-face slot threadIdx.x
+    // is row ty, column tx.
+    const int f = threadIdx.x;
+    const bool own_x = y0 + ty < geo.ny && x0 + ((tx - ty) & (TX - 1)) <= geo.nx;
+    const bool own_y = x0 + tx < geo.nx && y0 + ty <= geo.ny;
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      if (face_point(xL + g * NC * NFX + f, xR + g * NC * NFX + f, NFX, true) && own_x) ++nbad;
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      if (face_point(yB + g * NC * NFY + f, yT + g * NC * NFY + f, NFY, false) && own_y) ++nbad;
+  }
+  for (int e = threadIdx.x; e < 4 * (TX + TY); e += NT) {
+    if (e < 4 * TY) {  // x-faces of column TX, row r
+      const int g = e / TY, r = e % TY, f = TX * TY + r;
+      if (face_point(xL + g * NC * NFX + f, xR + g * NC * NFX + f, NFX, true) && y0 + r < geo.ny &&
+          x0 + TX == geo.nx)
+        ++nbad;
+    } else {  // y-faces of row TY, column col
+      const int q = e - 4 * TY, g = q / TX, col = q % TX, f = TX * TY + col;
+      if (face_point(yB + g * NC * NFY + f, yT + g * NC * NFY + f, NFY, false) && x0 + col < geo.nx &&
+          y0 + TY == geo.ny)
+        ++nbad;
     }
   }
   warp_count_add(ntrace, nbad);
