@@ -54,13 +54,15 @@ __device__ __forceinline__ int ghost_images(int i, int n, int lo, int hi, int sg
   return q;
 }
 
+// Cells at least G away from every side have no ghost image (the common case).
+__device__ __forceinline__ bool has_ghost_images(const Geo& g, int j, int i) {
+  return i < G || i >= g.nx - G || (g.rows > 1 && (j < G || j >= g.ny - G));
+}
+
 // Write v to cell (i, j) of plane p and to every ghost image of that cell.
 template <typename T>
 __device__ __forceinline__ void store_with_ghosts(T* __restrict__ out, const Geo& g, int p, int j, int i, T v) {
-  // cells at least G away from every side have no image (the common case)
-  const bool near_x = i < G || i >= g.nx - G;
-  const bool near_y = g.rows > 1 && (j < G || j >= g.ny - G);
-  if (!(near_x || near_y)) {
+  if (!has_ghost_images(g, j, i)) {
     out[cell_index(g, p, j, i)] = v;
     return;
   }
@@ -130,6 +132,83 @@ __device__ __forceinline__ void gather_patch(const T* tile, int c, int hx, int h
     A[s] = pa[o];
     X[s] = px[o];
     Y[s] = py[o];
+  }
+}
+
+// Patch of moments of ring cell r of component c, mirrored / transposed so
+// that the trace the ring cell shows the tile is the right-face trace of the
+// patch (the rule in stage2d_tile); (rx, ry) receives the ring cell's tile
+// position.  Ring cells: rows first (bottom r < TX, top r < 2 TX), then
+// columns (left, right).  Rows run the patch's x along the tile's y (x- and
+// y-moments swapped), columns along the tile's x; the side only flips the
+// direction (and the sign of the new x-moment).  FP32 (COMPILE_TIME_STRIDES)
+// takes rows and columns on separate paths, whose offsets from three
+// pointers are compile-time constants: its ring tasks are padded so that a
+// warp holds rows or columns only.  FP64 takes one path with run-time
+// offsets (its warps mix rows and columns).
+template <typename T, int TX, int TY, int HX, int HY, bool COMPILE_TIME_STRIDES>
+__device__ __forceinline__ void ring_patch(const T* tile, int c, int r, T* A, T* X, T* Y, int& rx, int& ry) {
+  constexpr int P = HY * HX;  // plane stride
+  constexpr unsigned long long kSign = 0x8000000000000000ull;
+  if constexpr (COMPILE_TIME_STRIDES) {
+    if (r < 2 * TX) {
+      const bool top = r >= TX;
+      rx = top ? r - TX : r;
+      ry = top ? TY : -1;
+      const int s = top ? -HX : HX;  // the patch's x step (along the tile's y)
+      const unsigned long long m = top ? kSign : 0ull;
+      const T* pa = tile + (size_t)(c * 3) * P + (ry + 2) * HX + (rx + 2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* ra = pa + (a - 1) * s;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          A[b * 3 + a] = ra[b - 1];
+          X[b * 3 + a] = flip_sign(ra[(b - 1) + 2 * P], m);
+          Y[b * 3 + a] = ra[(b - 1) + P];
+        }
+      }
+    } else {
+      const bool right = r >= 2 * TX + TY;
+      rx = right ? TX : -1;
+      ry = right ? r - 2 * TX - TY : r - 2 * TX;
+      const int s = right ? -1 : 1;  // the patch's x step (along the tile's x)
+      const unsigned long long m = right ? kSign : 0ull;
+      const T* pa = tile + (size_t)(c * 3) * P + (ry + 2) * HX + (rx + 2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T* ra = pa + (a - 1) * s;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          A[b * 3 + a] = ra[(b - 1) * HX];
+          X[b * 3 + a] = flip_sign(ra[(b - 1) * HX + P], m);
+          Y[b * 3 + a] = ra[(b - 1) * HX + 2 * P];
+        }
+      }
+    }
+  } else {
+    int ox, oy, swap;
+    unsigned long long xsign;
+    if (r < TX) {
+      rx = r; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull;
+    } else if (r < 2 * TX) {
+      rx = r - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = kSign;
+    } else if (r < 2 * TX + TY) {
+      rx = -1; ry = r - 2 * TX; ox = 1; oy = HX; swap = 0; xsign = 0ull;
+    } else {
+      rx = TX; ry = r - 2 * TX - TY; ox = -1; oy = HX; swap = 0; xsign = kSign;
+    }
+    const int off = (ry + 2) * HX + (rx + 2);
+    const T* pa = tile + (size_t)(c * 3 + 0) * P + off;
+    const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * P + off;
+    const T* py = tile + (size_t)(c * 3 + (swap ? 1 : 2)) * P + off;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const int o = (q % 3 - 1) * ox + (q / 3 - 1) * oy;
+      A[q] = pa[o];
+      X[q] = flip_sign(px[o], xsign);
+      Y[q] = py[o];
+    }
   }
 }
 
@@ -315,46 +394,22 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   //   right ring cell  needs tr_xm = tr_xp of u(-x, y)       (x-moments change sign)
   //   bottom ring cell needs tr_yp = tr_xp of u(y, x)        (x- and y-moments swap)
   //   top ring cell    needs tr_ym = tr_xp of u(y, -x)       (swap; new x-moment = -old y-moment)
-  // with the Gauss points in the same ascending order.  All lanes run one
-  // code path; only the gather offsets differ.  Tasks run rows first, then
-  // columns; in FP32 each component's tasks are padded to whole warps, so
-  // that a warp gathers from one ring segment (a row: consecutive words; a
-  // column: rows HX apart) and its neighbour component's rows do not share
-  // its banks.  FP64 is not padded: an idle lane still costs its warp a
-  // full FP64 instruction.
+  // with the Gauss points in the same ascending order (the gather:
+  // ring_patch).  Tasks run rows first, then columns; in FP32 each
+  // component's tasks are padded to whole warps, so that a warp gathers from
+  // one ring segment (a row: consecutive words; a column: rows HX apart), its
+  // neighbour component's rows do not share its banks, and its gather
+  // offsets are compile-time constants.  FP64 is not padded: an idle lane
+  // still costs its warp a full FP64 instruction.
   {
     constexpr int NR = 2 * (TX + TY);
     constexpr int NRP = sizeof(T) == 4 ? (NR + 31) / 32 * 32 : NR;
     for (int task = threadIdx.x; task < NRP * NC; task += NT) {
       const int r = task % NRP, c = task / NRP;
       if (r >= NR) continue;
-      int rx, ry, ox, oy, swap, fstride;
-      unsigned long long xsign;
-      T* out;
-      if (r < TX) {  // bottom row: its top trace = bottom side of y-face 0
-        rx = r; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; fstride = NFY;
-        out = yB + YI(0, rx, 0, 0);
-      } else if (r < 2 * TX) {  // top row: its bottom trace = top side of y-face TY
-        rx = r - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; fstride = NFY;
-        out = yT + YI(TY, rx, 0, 0);
-      } else if (r < 2 * TX + TY) {  // left column: its right trace = left side of x-face 0
-        rx = -1; ry = r - 2 * TX; ox = 1; oy = HX; swap = 0; xsign = 0ull; fstride = NFX;
-        out = xL + XI(ry, 0, 0, 0);
-      } else {  // right column: its left trace = right side of x-face TX
-        rx = TX; ry = r - 2 * TX - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; fstride = NFX;
-        out = xR + XI(ry, TX, 0, 0);
-      }
-      const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + (ry + 2) * HX + (rx + 2);
-      const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * HY * HX + (ry + 2) * HX + (rx + 2);
-      const T* py = tile + (size_t)(c * 3 + (swap ? 1 : 2)) * HY * HX + (ry + 2) * HX + (rx + 2);
+      int rx, ry;
       T A[9], X[9], Y[9], t[4];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const int o = (q % 3 - 1) * ox + (q / 3 - 1) * oy;
-        A[q] = pa[o];
-        X[q] = flip_sign(px[o], xsign);
-        Y[q] = py[o];
-      }
+      ring_patch<T, TX, TY, HX, HY, sizeof(T) == 4>(tile, c, r, A, X, Y, rx, ry);
       Recon2D<K>::tr_xp(A, X, Y, t);
       if (theta != nullptr) {  // the ring cell's scaled reconstruction: u_bar + theta (t - u_bar)
         T tr, tt;
@@ -365,8 +420,19 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
           for (int g = 0; g < 4; ++g) t[g] = fma(th, t[g] - A[4], A[4]);
         }
       }
+      // bottom row: its top trace = bottom side of y-face 0; top row: its
+      // bottom trace = top side of y-face TY; left column: its right trace =
+      // left side of x-face 0; right column: its left trace = right side of
+      // x-face TX
+      if (r < 2 * TX) {
+        T* out = (r < TX ? yB + YI(0, rx, 0, c) : yT + YI(TY, rx, 0, c));
 #pragma unroll
-      for (int g = 0; g < 4; ++g) out[(g * NC + c) * fstride] = t[g];
+        for (int g = 0; g < 4; ++g) out[g * NC * NFY] = t[g];
+      } else {
+        T* out = (r < 2 * TX + TY ? xL + XI(ry, 0, 0, c) : xR + XI(ry, TX, 0, c));
+#pragma unroll
+        for (int g = 0; g < 4; ++g) out[g * NC * NFX] = t[g];
+      }
     }
   }
   __syncthreads();
@@ -441,6 +507,7 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
     hwx[g] = T(0.5 * famgen::kGaussW[g] * famgen::kGaussX[g]);
   }
   T vout[NC];  // this cell's output averages (the safeguard's stage check)
+  T vals[NC * 3];  // this cell's output moments, plane by plane
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const T* fl = xL + XI(ty, tx, 0, c);
@@ -478,8 +545,17 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
         }
       }
       if (m == 0) vout[c] = v;
-      store_with_ghosts(Uout, geo, p, j, i, v);
+      vals[p] = v;
     }
+  }
+  // one test for the cell's ghost images, then the 3 NC plain stores
+  if (!has_ghost_images(geo, j, i)) {
+    const long long q = cell_index(geo, 0, j, i);
+#pragma unroll
+    for (int p = 0; p < NC * 3; ++p) Uout[q + p * geo.plane] = vals[p];
+  } else {
+#pragma unroll
+    for (int p = 0; p < NC * 3; ++p) store_with_ghosts(Uout, geo, p, j, i, vals[p]);
   }
   // BP/PP safeguard: a stage output average outside the admissible set
   // discards the step (the OE then writes nothing; see FamCtl::stage_bad)
@@ -595,29 +671,12 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
   for (int task = threadIdx.x; task < NRP * NC; task += NT) {
     const int r = task % NRP, c = task / NRP;
     if (r >= NR) continue;
-    int rx, ry, ox, oy, swap, slot;
-    unsigned long long xsign;
-    if (r < TX) {  // bottom ring row: its top trace
-      rx = r; ry = -1; ox = HX; oy = 1; swap = 1; xsign = 0ull; slot = 3;
-    } else if (r < 2 * TX) {  // top ring row: its bottom trace
-      rx = r - TX; ry = TY; ox = -HX; oy = 1; swap = 1; xsign = 0x8000000000000000ull; slot = 2;
-    } else if (r < 2 * TX + TY) {  // left ring column: its right trace
-      rx = -1; ry = r - 2 * TX; ox = 1; oy = HX; swap = 0; xsign = 0ull; slot = 1;
-    } else {  // right ring column: its left trace
-      rx = TX; ry = r - 2 * TX - TY; ox = -1; oy = HX; swap = 0; xsign = 0x8000000000000000ull; slot = 0;
-    }
-    const int off = (ry + 2) * HX + (rx + 2);
-    const T* pa = tile + (size_t)(c * 3 + 0) * HY * HX + off;
-    const T* px = tile + (size_t)(c * 3 + (swap ? 2 : 1)) * HY * HX + off;
-    const T* py = tile + (size_t)(c * 3 + (swap ? 1 : 2)) * HY * HX + off;
+    // bottom ring row: its top trace (slot 3); top row: its bottom trace (2);
+    // left column: its right trace (1); right column: its left trace (0)
+    const int slot = r < TX ? 3 : r < 2 * TX ? 2 : r < 2 * TX + TY ? 1 : 0;
+    int rx, ry;
     T A[9], X[9], Y[9], t[4];
-#pragma unroll
-    for (int s2 = 0; s2 < 9; ++s2) {
-      const int o = (s2 % 3 - 1) * ox + (s2 / 3 - 1) * oy;
-      A[s2] = pa[o];
-      X[s2] = flip_sign(px[o], xsign);
-      Y[s2] = py[o];
-    }
+    ring_patch<T, TX, TY, HX, HY, sizeof(T) == 4>(tile, c, r, A, X, Y, rx, ry);
     Recon2D<K>::facec(A, X, Y, t, q6);  // only t[1] (x = +1/2) is used
     const int q = (ry + 1) * RX + (rx + 1);
     fc[FI(slot, c, q)] = t[1];
@@ -695,7 +754,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
     // (products on the integer pipes: pmul, bit-identical to the FP64 unit's)
     const T theta = fma(pmul(bx, sig_x), dt_idx, pmul(pmul(by, sig_y), dt_idy));
     const T delta = Fast<T>::exp_(-theta);
-    T uavg[NC];
+    T uavg[NC], vals[NC * 3];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const T a = tile[(size_t)(c * 3) * HY * HX + hy * HX + hx];
@@ -703,9 +762,17 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
       const T m1 = pmul(tile[(size_t)(c * 3 + 1) * HY * HX + hy * HX + hx], delta);
       const T m2 = pmul(tile[(size_t)(c * 3 + 2) * HY * HX + hy * HX + hx], delta);
       if (!finite_bits(a) || !finite_bits(m1) || !finite_bits(m2)) ok = false;
-      store_with_ghosts(Uout, geo, c * 3 + 0, j, i, a);
-      store_with_ghosts(Uout, geo, c * 3 + 1, j, i, m1);
-      store_with_ghosts(Uout, geo, c * 3 + 2, j, i, m2);
+      vals[c * 3 + 0] = a;
+      vals[c * 3 + 1] = m1;
+      vals[c * 3 + 2] = m2;
+    }
+    if (!has_ghost_images(geo, j, i)) {
+      const long long qc = cell_index(geo, 0, j, i);
+#pragma unroll
+      for (int p = 0; p < NC * 3; ++p) Uout[qc + p * geo.plane] = vals[p];
+    } else {
+#pragma unroll
+      for (int p = 0; p < NC * 3; ++p) store_with_ghosts(Uout, geo, p, j, i, vals[p]);
     }
     if (!ok) atomicOr(status, kStatusNonFinite);
     else if (!ph.admissible(uavg)) atomicOr(status, kStatusNonPhysical);
