@@ -52,13 +52,14 @@ UNIT = "cell-stage/s"
 # FLOP fewer per cell).
 FLOP_PER_CELL_STAGE = {(5, 64): 2847.2, (5, 32): 2847.2}
 # FP64-unit instructions (DFMA + DADD + DMUL) per cell of one stage launch,
-# counted by ncu on the same capture: the FP64 unit's own busy fraction is
-# these at one instruction per FP64 lane and cycle (half the FLOP peak).
-FP64_UNIT_INST_PER_CELL = {(5, 64): 1793.8}
+# counted by ncu on the current kernel (2048^2 FAM5, 16x8 tiles: 1071.0 DFMA
+# + 485.2 DADD + 200.5 DMUL): the FP64 unit's own busy fraction is these at
+# one instruction per FP64 lane and cycle (half the FLOP peak).
+FP64_UNIT_INST_PER_CELL = {(5, 64): 1756.7}
 # DRAM bytes per launch of the stage kernel per cell (dram__bytes_read.sum +
-# dram__bytes_write.sum of the current kernel, 1.1833 GB / 4.19 M cells);
+# dram__bytes_write.sum of the current kernel, 1.1847 GB / 4.19 M cells);
 # traffic grows with the cell count, so it scales to the 4096^2 launch.
-DRAM_BYTES_PER_CELL = {(5, 64): 282.1}
+DRAM_BYTES_PER_CELL = {(5, 64): 282.5}
 
 
 def parse():
@@ -455,7 +456,7 @@ def batched2d_report(a, torch, prec: int = 64):
 # tiles), counted by ncu (smsp__inst_executed.sum / cells at 2048^2,
 # profiles/stage2d_k5_f32_2048.md): the FP32 stage is issue-bound, so its
 # roofline is the issue rate, one warp instruction per cycle per scheduler.
-FP32_STAGE_WARP_INST_PER_CELL = {5: 96.7}
+FP32_STAGE_WARP_INST_PER_CELL = {5: 83.76}
 
 
 def _sm_clock_hz() -> float:
