@@ -785,7 +785,7 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
 // that 6 CTAs of 128 threads fit.
 template <typename T, int NT>
 constexpr int oe_min_blocks() {
-  return sizeof(T) == 8 ? 1 : (768 / NT);
+  return sizeof(T) == 8 ? 1 : (1024 / NT);
 }
 
 template <typename T, int K, class PH, int TX, int TY>
