@@ -781,8 +781,10 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
   }
 }
 
-// Resident CTAs per SM of the OE kernel: FP32 keeps its registers at 80 so
-// that 6 CTAs of 128 threads fit.
+// Resident CTAs per SM of the OE kernel: FP32 keeps its registers at 64 so
+// that 32 warps fit (8 CTAs of 128 threads, 4 of 256; 12 bytes spill).  At
+// 24 warps the 4096^2 FAM5 OE took 1.06 ms, at 32 warps 0.90 ms; at 40
+// warps (48 registers) it would spill 60-72 bytes.
 template <typename T, int NT>
 constexpr int oe_min_blocks() {
   return sizeof(T) == 8 ? 1 : (1024 / NT);
