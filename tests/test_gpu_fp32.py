@@ -123,3 +123,41 @@ def test_euler_2d_fp32_error_against_oracle(k, data):
         assert e < 1e-5 and e1 < 1e-5
     else:
         assert e < 0.1 and e1 < 1e-3
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("bc", ["periodic", "outflow"])
+def test_residual_and_oe_2d_fp32_every_tile_shape(tile, k, bc):
+    """FP32 residual and OE on a ragged 70 x 45 grid with each 2D tile shape
+    (32x8, 32x4, 16x8: several tiles, partial ones at the far sides, ring
+    cells in every direction), against the oracle.  The bars are multiples
+    of the change the oracle's own result shows when its input is rounded to
+    FP32 (residual) or perturbed by FP32-ulp noise (OE, whose input is the
+    rounded state), measured on the same data (measured: up to 6.7x for the
+    residual, 3.1x for the OE; bar 50x); a ring trace gathered from a wrong
+    plane, side or sign moves the tile-edge cells by 1e-2 or more."""
+    from test_gpu_parity import comp_err, plane_err, smooth_state
+    n = (70, 45)
+    s, P = make(2, n, k, "euler", bc, prec=32, tile2d=tile)
+    U = smooth_state(2, n, seed=3, amp=0.25)
+    # rough moments, so that the OE damps (median theta 0.4 to 1.2)
+    U[:, 1:] += 2e-3 * np.random.default_rng(7).standard_normal(U[:, 1:].shape)
+    U32 = U.astype(np.float32)
+    Ur = U32.astype(np.float64)
+    want = oracle.residual(P, U)
+    spread = comp_err(oracle.residual(P, Ur), want)
+    e = comp_err(s.residual(U32), want)
+    dt = 0.7 / n[0]
+    want_oe, theta = oracle.oe(P, dt, Ur)
+    Up = Ur * (1.0 + 2.0 ** -24 * np.random.default_rng(1).standard_normal(Ur.shape))
+    spread_oe = plane_err(oracle.oe(P, dt, Up)[0], want_oe)
+    got_oe = s.oe(dt, U32)
+    e_oe = plane_err(got_oe, want_oe)
+    s.close()
+    print(f"\nFP32 tile {tile} k={k} {bc}: residual {e:.2e} ({e / spread:.1f}x spread), "
+          f"OE {e_oe:.2e} ({e_oe / spread_oe:.1f}x spread)")
+    assert np.median(theta) > 0.3
+    assert np.array_equal(got_oe[:, 0], U32[:, 0])  # averages exact
+    assert e < 50.0 * spread, (e, spread)
+    assert e_oe < 50.0 * spread_oe, (e_oe, spread_oe)
