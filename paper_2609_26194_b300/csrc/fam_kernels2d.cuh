@@ -1083,19 +1083,36 @@ __global__ void __launch_bounds__(NT, pp_min_blocks<T, NT>()) pp_theta2d(const T
     double px = 0.0, py = 0.0;  // this cell's speed maxima, published for the screen of later cells
     double seen_x = 0.0, seen_y = 0.0;  // the grid maxima this thread read
     if (q < n) {
-      const int i = (int)(q % wx) - 1, j = (int)(q / wx) - 1;
+      // (32-bit division whenever the cell count allows it: the branch is
+      // uniform over the launch)
+      int i, j;
+      if (n <= 0xffffffffll) {
+        const unsigned int uq = (unsigned int)q, uj = uq / (unsigned int)wx;
+        j = (int)uj - 1;
+        i = (int)(uq - uj * (unsigned int)wx) - 1;
+      } else {
+        j = (int)(q / wx) - 1;
+        i = (int)(q - (long long)(j + 1) * wx) - 1;
+      }
+      // the 3x3 patch: one 64-bit plane base per plane, 32-bit offsets
+      // within it (rows of the padded layout)
+      const T* centre = U + cell_index(geo, 0, j, i);
+      const int pitch = geo.px;
       // coefficients: deviation bounds and the average here; a copy in this
       // thread's shared-memory slot for the cells whose points are needed
       T avg[NC], d[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         T A[9], X[9], Y[9], cf[NCOEF];
+        const T* pa = centre + (long long)(c * 3) * geo.plane;
+        const T* pmx = pa + geo.plane;
+        const T* pmy = pmx + geo.plane;
 #pragma unroll
         for (int s9 = 0; s9 < 9; ++s9) {
-          const int ii = i + s9 % 3 - 1, jj = j + s9 / 3 - 1;
-          A[s9] = U[cell_index(geo, c * 3 + 0, jj, ii)];
-          X[s9] = U[cell_index(geo, c * 3 + 1, jj, ii)];
-          Y[s9] = U[cell_index(geo, c * 3 + 2, jj, ii)];
+          const int o = (s9 / 3 - 1) * pitch + (s9 % 3 - 1);
+          A[s9] = pa[o];
+          X[s9] = pmx[o];
+          Y[s9] = pmy[o];
         }
         Recon2D<K>::coef(A, X, Y, cf);
         avg[c] = cf[0];
