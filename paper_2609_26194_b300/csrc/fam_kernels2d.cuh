@@ -212,6 +212,32 @@ __device__ __forceinline__ void ring_patch(const T* tile, int c, int r, T* A, T*
   }
 }
 
+// Ring task -> (ring cell r, component c).  FP32: the row tasks of every
+// component first (2 TX per component, a multiple of 32), then the column
+// tasks (2 TY per component), so that a warp holds rows or columns only and
+// no lane idles.  FP64: component by component.
+template <typename T, int TX, int TY, int NC>
+struct RingTasks {
+  static constexpr int NR = 2 * (TX + TY);
+  static constexpr int count = NR * NC;
+  static_assert(sizeof(T) != 4 || (2 * TX * NC) % 32 == 0, "FP32 row tasks must fill whole warps");
+  __device__ __forceinline__ static void of(int task, int& r, int& c) {
+    if constexpr (sizeof(T) == 4) {
+      if (task < 2 * TX * NC) {
+        c = task / (2 * TX);
+        r = task % (2 * TX);
+      } else {
+        const int q = task - 2 * TX * NC;
+        c = q / (2 * TY);
+        r = 2 * TX + q % (2 * TY);
+      }
+    } else {
+      c = task / NR;
+      r = task % NR;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // stage kernel
 // ---------------------------------------------------------------------------
@@ -395,18 +421,15 @@ __device__ __forceinline__ void stage2d_tile(const T* __restrict__ tile, T* xL, 
   //   bottom ring cell needs tr_yp = tr_xp of u(y, x)        (x- and y-moments swap)
   //   top ring cell    needs tr_ym = tr_xp of u(y, -x)       (swap; new x-moment = -old y-moment)
   // with the Gauss points in the same ascending order (the gather:
-  // ring_patch).  Tasks run rows first, then columns; in FP32 each
-  // component's tasks are padded to whole warps, so that a warp gathers from
-  // one ring segment (a row: consecutive words; a column: rows HX apart), its
-  // neighbour component's rows do not share its banks, and its gather
-  // offsets are compile-time constants.  FP64 is not padded: an idle lane
-  // still costs its warp a full FP64 instruction.
+  // ring_patch).  In FP32 the row tasks of all components come first, then
+  // the column tasks (RingTasks): a warp gathers from one ring segment of
+  // rows (consecutive words) or from columns (rows HX apart), with
+  // compile-time offsets, and no lane idles.
   {
-    constexpr int NR = 2 * (TX + TY);
-    constexpr int NRP = sizeof(T) == 4 ? (NR + 31) / 32 * 32 : NR;
-    for (int task = threadIdx.x; task < NRP * NC; task += NT) {
-      const int r = task % NRP, c = task / NRP;
-      if (r >= NR) continue;
+    using RT = RingTasks<T, TX, TY, NC>;
+    for (int task = threadIdx.x; task < RT::count; task += NT) {
+      int r, c;
+      RT::of(task, r, c);
       int rx, ry;
       T A[9], X[9], Y[9], t[4];
       ring_patch<T, TX, TY, HX, HY, sizeof(T) == 4>(tile, c, r, A, X, Y, rx, ry);
@@ -654,7 +677,6 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
   // the one trace each ring cell shows the tile, evaluated as the right-face
   // trace of a mirrored / transposed patch (as in stage2d); the Rusanov
   // speeds at the averages of the tile and its ring (corners included).
-  constexpr int NR = 2 * (TX + TY);
   for (int task = threadIdx.x; task < TX * TY * NC; task += NT) {
     const int cell = task % (TX * TY), c = task / (TX * TY);
     const int cx = cell % TX, cy = cell / TX;
@@ -666,7 +688,9 @@ __device__ __forceinline__ void oe2d_tile(const T* __restrict__ tile, T* fc, T* 
     for (int f = 0; f < 4; ++f) fc[FI(f, c, q)] = t[f];
   }
   // rows first, then columns; FP32 pads each component's tasks to whole
-  // warps (one ring segment per warp, as in stage2d_tile)
+  // warps, so that a warp holds rows or columns only (the stage's order,
+  // RingTasks, left this kernel 16 more bytes of spills at 64 registers)
+  constexpr int NR = 2 * (TX + TY);
   constexpr int NRP = sizeof(T) == 4 ? (NR + 31) / 32 * 32 : NR;
   for (int task = threadIdx.x; task < NRP * NC; task += NT) {
     const int r = task % NRP, c = task / NRP;
