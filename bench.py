@@ -456,7 +456,7 @@ def batched2d_report(a, torch, prec: int = 64):
 # tiles), counted by ncu (smsp__inst_executed.sum / cells at 2048^2,
 # profiles/stage2d_k5_f32_2048.md): the FP32 stage is issue-bound, so its
 # roofline is the issue rate, one warp instruction per cycle per scheduler.
-FP32_STAGE_WARP_INST_PER_CELL = {5: 83.76}
+FP32_STAGE_WARP_INST_PER_CELL = {5: 82.16}
 
 
 def _sm_clock_hz() -> float:
