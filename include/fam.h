@@ -355,9 +355,10 @@ fam_status fam_batch_info(fam_batch_t h, int* tile_x, int* grid, long* ntiles, l
 fam_status fam_batch_tile(fam_batch_t h, int* tile_x, int* tile_y);
 /* Autotuner: times probe_steps steps for each tile shape (1D widths 64,
  * 128, 256; 2D 32x8, 32x4, 16x8) and blocks-per-SM choice on the handle's
- * current state (restored afterwards), keeps the fastest, and appends it to
- * cache_path (if not NULL) keyed by GPU name and problem; a cached entry is
- * reused without timing.  *tile_x receives the tile's x extent. */
+ * current state (restored afterwards, clocks included), keeps the fastest, and appends it to
+ * cache_path (if not NULL) keyed by GPU name, problem and the safeguard; a
+ * cached entry is reused without timing.  *tile_x receives the tile's x
+ * extent. */
 fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char* cache_path, int* tile_x,
                           int* blocks_per_sm);
 const char* fam_batch_last_error(fam_batch_t h);

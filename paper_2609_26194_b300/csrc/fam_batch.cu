@@ -813,7 +813,8 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
   std::ostringstream key;
-  key << prop.name << "|d" << h->d << "|eq" << h->eq << "|p" << h->prec << "|n" << h->n << "|cells" << h->cells;
+  key << prop.name << "|d" << h->d << "|eq" << h->eq << "|p" << h->prec << "|n" << h->n << "|cells" << h->cells
+      << (h->pp ? "|pp" : "");
   // candidate tile shapes: 1D tile widths, 2D indices into kBatchTile2D
   auto& shape = h->d == 1 ? h->tile_x : h->tile2d;
   if (cache_path && cache_path[0]) {
@@ -835,10 +836,15 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
       }
     }
   }
-  // save the state, time each candidate from the same state, restore
+  // save the state and the clocks, time each candidate from the same state,
+  // restore both
   void* save = nullptr;
-  FAMB_CUDA(h, cudaMalloc(&save, h->total * h->elem));
+  FAMB_CUDA(h, cudaMalloc(&save, h->total * h->elem + sizeof(BatchCtl) * h->n + sizeof(BatchGlobal)));
+  BatchCtl* save_ctl = reinterpret_cast<BatchCtl*>(static_cast<char*>(save) + h->total * h->elem);
+  BatchGlobal* save_glob = reinterpret_cast<BatchGlobal*>(save_ctl + h->n);
   FAMB_CUDA(h, cudaMemcpyAsync(save, h->buf[0], h->total * h->elem, cudaMemcpyDeviceToDevice, h->stream));
+  FAMB_CUDA(h, cudaMemcpyAsync(save_ctl, h->ictl, sizeof(BatchCtl) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  FAMB_CUDA(h, cudaMemcpyAsync(save_glob, h->glob, sizeof(BatchGlobal), cudaMemcpyDeviceToDevice, h->stream));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -879,7 +885,8 @@ fam_status fam_batch_tune(fam_batch_t h, double cfl, int probe_steps, const char
   h->blocks_per_sm = best_b;
   fam_status s = build_tiles(h);
   FAMB_CUDA(h, cudaMemcpyAsync(h->buf[0], save, h->total * h->elem, cudaMemcpyDeviceToDevice, h->stream));
-  reset_clock(h);
+  FAMB_CUDA(h, cudaMemcpyAsync(h->ictl, save_ctl, sizeof(BatchCtl) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  FAMB_CUDA(h, cudaMemcpyAsync(h->glob, save_glob, sizeof(BatchGlobal), cudaMemcpyDeviceToDevice, h->stream));
   FAMB_CUDA(h, cudaStreamSynchronize(h->stream));
   cudaFree(save);
   h->dt_valid = false;

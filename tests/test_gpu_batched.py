@@ -74,8 +74,14 @@ def test_batch_riemann_instances_and_tuner():
     b.run(20, 0.3)
     b.sync()
     ref = b.get_state()
+    clock = b.times()
     tx, bps = b.tune(0.3, probe_steps=2)
     assert tx in (64, 128, 256) and bps >= 1
+    # the tuner restores the state and every instance's clock
+    for r, a in zip(ref, b.get_state()):
+        assert np.array_equal(r, a)
+    for before, after in zip(clock, b.times()):
+        assert np.array_equal(before, after)
     b.set_state(states)
     b.run(20, 0.3)
     b.sync()
